@@ -1,0 +1,146 @@
+"""Seeded synthetic inputs for the hysteresis workloads (shared by tests, bench and oracle checks).
+
+This module only *generates* inputs: grids, material constants, initial
+magnetisations and field sweeps.  It contains none of the method's
+arithmetic, so the CUDA library and the CPU oracle can both be fed from it
+without sharing any computation.
+
+Random numbers come from SplitMix64 (Steele, Lea, Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014), written out here so the same
+seed gives the same bits on every machine and numpy version.
+
+Workloads follow the thin-film geometry and material of muMAG Standard
+Problem #1 as the paper gives them (Section 4: Ms = 8e5 A/m, A = 1.3e-11 J/m,
+K = 500 J/m^3, easy axis along the long edge, field tilted 1 degree in plane,
+1 mT field steps).  The paper's own runs used the SP1 film; only its geometry
+and constants are used here, as synthetic stand-ins.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+MU0 = 4e-7 * math.pi  # used only to express field values given in tesla as A/m
+
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def splitmix64(seed: int, n: int) -> np.ndarray:
+    """n outputs of SplitMix64 started from ``seed`` (uint64 array)."""
+    with np.errstate(over="ignore"):
+        idx = np.arange(1, n + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + idx * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform(seed: int, n: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+    """n doubles uniform in [lo, hi) from the top 53 bits of SplitMix64."""
+    u = (splitmix64(seed, n) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    return lo + (hi - lo) * u
+
+
+def _unit(v: np.ndarray) -> np.ndarray:
+    return v / np.sqrt(np.sum(v * v, axis=0, keepdims=True))
+
+
+def tilted_uniform_m(shape, seed: int, axis=(1.0, 0.0, 0.0), amplitude: float = 1e-3) -> np.ndarray:
+    """Unit field (3, nz, ny, nx): normalize(axis + amplitude * xi), xi uniform in [-1,1]^3."""
+    nz, ny, nx = shape
+    xi = uniform(seed, 3 * nx * ny * nz, -1.0, 1.0).reshape(3, nz, ny, nx)
+    v = np.asarray(axis, dtype=np.float64).reshape(3, 1, 1, 1) + amplitude * xi
+    return np.ascontiguousarray(_unit(v))
+
+
+def random_unit_m(shape, seed: int) -> np.ndarray:
+    """Unit field (3, nz, ny, nx) with directions uniform on the sphere
+    (z uniform in [-1,1], azimuth uniform)."""
+    nz, ny, nx = shape
+    n = nx * ny * nz
+    u = uniform(seed, 2 * n)
+    z = 2.0 * u[:n] - 1.0
+    phi = 2.0 * math.pi * u[n:]
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    m = np.stack([r * np.cos(phi), r * np.sin(phi), z]).reshape(3, nz, ny, nx)
+    return np.ascontiguousarray(m)
+
+
+def field_direction(tilt_deg: float = 1.0) -> np.ndarray:
+    """In-plane unit vector tilted ``tilt_deg`` from +x toward +y."""
+    t = math.radians(tilt_deg)
+    return np.array([math.cos(t), math.sin(t), 0.0])
+
+
+def sp1_sweep(max_mT: float = 50.0, step_mT: float = 1.0, tilt_deg: float = 1.0) -> np.ndarray:
+    """Field values (n, 3) in A/m: descending +max..-max, then ascending
+    -max+step..+max, along the tilted direction (201 values for 50 mT / 1 mT)."""
+    n = int(round(max_mT / step_mT))
+    desc = [max_mT - step_mT * i for i in range(2 * n + 1)]
+    asc = [-max_mT + step_mT * i for i in range(1, 2 * n + 1)]
+    b = np.array(desc + asc) * 1e-3  # tesla
+    return np.outer(b / MU0, field_direction(tilt_deg))
+
+
+@dataclasses.dataclass
+class Workload:
+    """One synthetic workload: grid, material and sweep (SI units)."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    dy: float
+    dz: float
+    Ms: float = 8.0e5
+    A: float = 1.3e-11
+    K: float = 500.0
+    u: tuple = (1.0, 0.0, 0.0)
+    tol: float = 1e-5
+    seed: int = 1405
+    max_mT: float = 50.0
+    step_mT: float = 1.0
+    tilt_deg: float = 1.0
+    K_cell: np.ndarray | None = None  # per-cell K (nz, ny, nx) or None
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def ncells(self):
+        return self.nx * self.ny * self.nz
+
+    def initial_m(self) -> np.ndarray:
+        return tilted_uniform_m(self.shape, self.seed)
+
+    def fields(self) -> np.ndarray:
+        return sp1_sweep(self.max_mT, self.step_mT, self.tilt_deg)
+
+
+def film_32x16x1() -> Workload:
+    """1000 x 500 x 20 nm film on 32 x 16 x 1 cells (31.25 x 31.25 x 20 nm)."""
+    return Workload("film_32x16x1", 32, 16, 1, 31.25e-9, 31.25e-9, 20e-9)
+
+
+def film_512x256x4() -> Workload:
+    """2000 x 1000 x 20 nm film on 512 x 256 x 4 cells (3.90625 x 3.90625 x 5 nm);
+    padded FFT grid 1024 x 512 x 8."""
+    return Workload("film_512x256x4", 512, 256, 4, 2000e-9 / 512, 1000e-9 / 256, 5e-9)
+
+
+def film_128x64x2_random_K() -> Workload:
+    """500 x 250 x 10 nm film on 128 x 64 x 2 cells, per-cell K uniform in [300, 700] J/m^3."""
+    w = Workload("film_128x64x2_randK", 128, 64, 2, 500e-9 / 128, 250e-9 / 64, 5e-9)
+    w.K_cell = uniform(w.seed, w.ncells, 300.0, 700.0).reshape(w.shape)
+    return w
+
+
+WORKLOADS = {
+    "film_32x16x1": film_32x16x1,
+    "film_512x256x4": film_512x256x4,
+    "film_128x64x2_randK": film_128x64x2_random_K,
+}

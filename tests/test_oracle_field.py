@@ -1,0 +1,111 @@
+"""Pins of the oracle's effective field and energy.
+
+* FFT demag equals the direct O(N^2) sum with the same tensor (tiny and ragged grids).
+* Uniform magnetisation: the mean demag field is -Ms N_body m (body-sum identity).
+* Exchange: zero for uniform m; the closed form of a planar spiral.
+* Every term: H_i = -(1/(mu0 Ms V)) dU/dm_i by central finite differences of
+  the separately coded energy (pins the 1/2 of the demag energy, factors of 2
+  and signs of every term).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import micromag as om
+from paper_1405_2728_gb300 import inputs
+
+
+def _prob(nx, ny, nz, cell=(3.0e-9, 4.0e-9, 5.0e-9), K=500.0, u=(1.0, 0.0, 0.0)):
+    return om.Problem(nx, ny, nz, *cell, Ms=8.0e5, A=1.3e-11, K=K, u=u)
+
+
+@pytest.mark.parametrize("grid", [(1, 1, 1), (2, 1, 1), (1, 3, 1), (3, 2, 1), (2, 2, 2), (5, 3, 2), (7, 5, 3), (4, 1, 6)])
+def test_fft_demag_equals_direct_sum(grid):
+    prob = _prob(*grid)
+    m = inputs.random_unit_m(prob.shape, seed=11 + sum(grid))
+    full = om.newell_full(prob)
+    d = om.Demag(prob, full, workers=1)
+    Hf = d.field(m)
+    Hd = om.demag_direct(prob, m, full)
+    assert np.linalg.norm(Hf - Hd) <= 1e-13 * np.linalg.norm(Hd)
+
+
+def test_sampled_direct_cells_match_full_direct():
+    prob = _prob(6, 4, 3)
+    m = inputs.random_unit_m(prob.shape, seed=3)
+    full = om.newell_full(prob)
+    Hd = om.demag_direct(prob, m, full)
+    cells = [0, 5, 17, 40, 71]
+    Hs = om.demag_direct(prob, m, full, cells=cells)
+    assert np.allclose(Hs, Hd.reshape(3, -1)[:, cells], rtol=0, atol=1e-9)
+
+
+def test_uniform_m_mean_demag_is_body_factor():
+    prob = _prob(6, 5, 2)
+    mdir = np.array([0.6, -0.48, 0.64])
+    m = np.broadcast_to(mdir.reshape(3, 1, 1, 1), (3,) + prob.shape).copy()
+    H = om.Demag(prob, workers=1).field(m)
+    Nb = om.newell_entry(0, 0, 0, prob.nx * prob.dx, prob.ny * prob.dy, prob.nz * prob.dz)
+    Nmat = np.array([[Nb[0], Nb[3], Nb[4]], [Nb[3], Nb[1], Nb[5]], [Nb[4], Nb[5], Nb[2]]])
+    mean = H.reshape(3, -1).mean(axis=1)
+    assert np.allclose(mean, -prob.Ms * Nmat @ mdir, rtol=1e-12, atol=1e-9)
+
+
+def test_exchange_vanishes_for_uniform_m():
+    prob = _prob(6, 4, 3)
+    m = np.zeros((3,) + prob.shape)
+    m[2] = 1.0
+    assert np.all(om.exchange_field(prob, m) == 0)
+    assert om.energy(prob, m, (0, 0, 0), om.Demag(prob, workers=1))["exchange"] == 0.0
+
+
+def test_exchange_spiral_closed_form():
+    nx, ny, nz = 16, 3, 2
+    prob = _prob(nx, ny, nz, K=0.0)
+    q = 0.3  # rotation per cell (rad)
+    ang = q * np.arange(nx)
+    m = np.zeros((3,) + prob.shape)
+    m[0] = np.cos(ang)[None, None, :]
+    m[1] = np.sin(ang)[None, None, :]
+    E = om.energy(prob, m, (0, 0, 0), om.Demag(prob, workers=1))["exchange"]
+    expect = prob.A * prob.V * (nx - 1) * ny * nz * (2 - 2 * math.cos(q)) / prob.dx**2
+    assert abs(E - expect) <= 1e-13 * expect
+    H = om.exchange_field(prob, m)
+    c = 2 * prob.A / (om.MU0 * prob.Ms) * (2 * math.cos(q) - 2) / prob.dx**2
+    assert np.allclose(H[:, :, :, 1:-1], c * m[:, :, :, 1:-1], rtol=1e-12, atol=1e-6)
+
+
+def test_anisotropy_and_zeeman_closed_forms():
+    prob = _prob(2, 2, 1, K=1234.0, u=(0.0, 0.6, 0.8))
+    m = inputs.random_unit_m(prob.shape, 5)
+    Ha = om.anisotropy_field(prob, m)
+    mu = 0.6 * m[1] + 0.8 * m[2]
+    assert np.allclose(Ha[1], 2 * 1234.0 / (om.MU0 * prob.Ms) * mu * 0.6, rtol=1e-14)
+    E = om.energy(prob, m, (100.0, -50.0, 7.0), om.Demag(prob, workers=1))
+    assert abs(E["anisotropy"] - np.sum(1234.0 * prob.V * (1 - mu**2))) < 1e-14 * abs(E["anisotropy"])
+    zexp = -om.MU0 * prob.Ms * prob.V * np.sum(100.0 * m[0] - 50.0 * m[1] + 7.0 * m[2])
+    assert abs(E["zeeman"] - zexp) < 1e-14 * abs(zexp)
+
+
+@pytest.mark.parametrize("percell", [False, True])
+def test_field_is_energy_gradient(percell):
+    # H_i = -(1/(mu0 Ms V)) dU/dm_i, checked by central differences of U.
+    prob = _prob(5, 4, 2, K=3.0e4)
+    if percell:
+        prob.K = inputs.uniform(9, 40, 1e4, 5e4).reshape(prob.shape)
+        u = inputs.random_unit_m(prob.shape, 21)
+        prob.u = u
+    m = inputs.random_unit_m(prob.shape, 4)
+    Hext = np.array([2.0e4, -1.0e4, 5.0e3])
+    d = om.Demag(prob, workers=1)
+    H = om.heff(prob, m, Hext, d)
+    rng = np.random.default_rng(1)
+    h = 1e-6
+    for _ in range(10):
+        a, k, j, i = rng.integers(3), rng.integers(prob.nz), rng.integers(prob.ny), rng.integers(prob.nx)
+        mp = m.copy(); mp[a, k, j, i] += h
+        mm = m.copy(); mm[a, k, j, i] -= h
+        dU = (om.energy(prob, mp, Hext, d)["total"] - om.energy(prob, mm, Hext, d)["total"]) / (2 * h)
+        Hfd = -dU / (om.MU0 * prob.Ms * prob.V)
+        assert abs(Hfd - H[a, k, j, i]) <= 1e-7 * np.max(np.abs(H))
