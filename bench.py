@@ -1,0 +1,381 @@
+"""Benchmark: H_eff evaluations per second of the energy-minimising hysteresis
+sweep on the 2000 x 1000 x 20 nm film (512 x 256 x 4 cells), one GB300.
+
+A step is one field value of the sweep: set the field, minimise to the stop
+rule (max |m x H| / Ms < 1e-5) from the previous state -- the whole device
+path: x-FFT with the fused step, y-z convolution, x-inverse with the local
+terms and BB sums, the one-CTA step-size kernel, looped on the device by a CUDA
+graph.  `value` = effective-field evaluations per second over the K timed
+steps (inputs resident in HBM), L2 flushed between steps.  `e2e` is the same
+through the C ABI with the magnetisation in pinned host memory (copied in and
+out inside every step).  Under torchrun each rank runs an independent replica
+(a single minimisation does not shard); value sums the ranks' evaluations over
+the slowest rank's time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
+  python bench.py --impl reference   # the CPU oracle on the same workload and metric
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "H_eff evals/s & hysteresis-loop time (512x256x4 film) FP32 vs FP64, %HBM peak"
+UNIT = "H_eff evals/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 FMA lanes per SM per clock on GB300 (1.25 TFLOP/s at 2070 MHz over 152 SMs, 2 flops per FMA)
+FP64_FMA_PER_SM_CLK = 2
+FP32_FMA_PER_SM_CLK = 128
+N_SM = 152
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_model(info, esz):
+    """Bytes and flops per launch of each kernel stage (pass model; see the design notes).
+
+    Bytes: compulsory traffic of the pass structure -- xfwd reads m_k and g_k
+    and writes m_{k+1} and the x-spectrum; yz reads/writes the spectrum and
+    reads the tensor spectra; xinv reads the spectrum, m_{k+1}, m_k and g_k and
+    writes g_{k+1}.  Flops: real arithmetic of the radix-8 Stockham transforms
+    with zero-padding pruning, the tensor product and the local terms."""
+    nx, ny, nz, Px, Py, Pz = (info[k] for k in ("nx", "ny", "nz", "px", "py", "pz"))
+    N = nx * ny * nz
+    F = 3 * N * esz
+    W = info["spectrum_bytes"]
+    T = info["tensor_bytes"]
+    Hx = Px // 2
+    C = Hx + 1
+
+    def fft_flops(L, half_in, half_out):
+        if L <= 1:
+            return 0
+        lg = L.bit_length() - 1
+        passes = []
+        if lg % 3 == 1:
+            passes.append(2)
+        elif lg % 3 == 2:
+            passes.append(4)
+        passes += [8] * (lg // 3)
+        if L < 8:
+            passes = [L]
+        dft = {2: (4, 0), 4: (16, 8), 8: (56, 40)}
+        fl = 0
+        ns = 1
+        for i, R in enumerate(passes):
+            full, pruned = dft[R]
+            fl += (L // R) * (pruned if (i == 0 and half_in) else full)
+            if ns > 1:
+                fl += (L // R) * (R - 1) * 6 * (0.5 if (i == len(passes) - 1 and half_out) else 1)
+            ns *= R
+        return fl
+
+    x_rows = 3 * ny * nz
+    unpack = 10 * C
+    f_xfwd = x_rows * (fft_flops(Hx, True, False) + unpack) + N * 3 * 8
+    f_xinv = x_rows * (fft_flops(Hx, False, True) + unpack) + N * 3 * 40
+    zf = 3 * (fft_flops(Pz, True, False) + fft_flops(Pz, False, False))
+    f_yz = C * (3 * nz * (fft_flops(Py, True, False) + fft_flops(Py, False, True)) + Py * (zf + Pz * 36))
+    return {
+        "xfwd_step": {"bytes": 3 * F + W, "flops": f_xfwd},
+        "yz_conv": {"bytes": 2 * W + T, "flops": f_yz},
+        "xinv_local": {"bytes": W + 4 * F, "flops": f_xinv},
+        "reduce_bb": {"bytes": 0, "flops": 0},
+    }
+
+
+def load_traffic(stage, workload, precision):
+    """dram bytes per launch from the committed ncu summary, if one matches."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}_{precision}.json")
+    try:
+        with open(path) as f:
+            return json.load(f).get(stage)
+    except (OSError, ValueError):
+        return None
+
+
+def oracle_rate(w, seconds_budget=15.0, max_evals=40):
+    """Oracle (float64 numpy/scipy, quad tensor) H_eff+step iterations per second
+    on a bounded sample of the workload, on this host's cores."""
+    from oracle import micromag as om
+    from paper_1405_2728_gb300 import inputs
+    oprob = om.Problem(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, Ms=w.Ms, A=w.A, K=w.K)
+    workers = os.cpu_count() or 1
+    demag = om.Demag(oprob, workers=workers)
+    m = w.initial_m()
+    H = w.fields()[0]
+    om.minimize(oprob, m, H, demag, tol=0.0, max_iter=0)  # warm (1 evaluation)
+    evals, t0 = 0, time.perf_counter()
+    n = 1
+    while evals < max_evals and time.perf_counter() - t0 < seconds_budget:
+        r = om.minimize(oprob, m, H, demag, tol=0.0, max_iter=n)
+        evals += r.heff_evals
+        m = r.m
+    dt = time.perf_counter() - t0
+    return evals / dt, evals, workers, dt
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    from paper_1405_2728_gb300 import inputs
+    w = inputs.WORKLOADS[args.workload]()
+    from oracle import micromag as om
+    oprob = om.Problem(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, Ms=w.Ms, A=w.A, K=w.K)
+    workers = os.cpu_count() or 1
+    demag = om.Demag(oprob, workers=workers)
+    m = w.initial_m()
+    H = w.fields()[0]
+    for _ in range(args.warmup):
+        m = om.minimize(oprob, m, H, demag, tol=0.0, max_iter=1).m
+    t0 = time.perf_counter()
+    evals = 0
+    for _ in range(args.steps):   # each step: one minimiser iteration (one evaluation + step)
+        r = om.minimize(oprob, m, H, demag, tol=0.0, max_iter=1)
+        m = r.m
+        evals += r.heff_evals - 1
+    dt = time.perf_counter() - t0
+    value = evals / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "cells": [w.nx, w.ny, w.nz], "precision": args.precision},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                             "sample": f"{args.steps} oracle minimiser iterations (H_eff + step) at {w.name}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--workload", default="film_512x256x4")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    ws, rank, local = dist_env()
+
+    import torch
+    import torch.distributed as dist
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1405_2728_gb300 import build as mmbuild
+    mmbuild.build()
+    from paper_1405_2728_gb300 import inputs, mm
+
+    w = inputs.WORKLOADS[args.workload]()
+    prec = mm.MM_FP64 if args.precision == "fp64" else mm.MM_FP32
+    tdt = torch.float64 if prec == mm.MM_FP64 else torch.float32
+    esz = 8 if prec == mm.MM_FP64 else 4
+    grid = mm.make_grid(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz)
+    prob = mm.mm_setup_geometry(grid, mm.make_material(w.Ms, w.A, w.K), prec)
+    info = mm.mm_problem_info(prob)
+    F = w.fields()
+    opts = mm.make_opts(tol=w.tol, max_iter=200000)
+    stream = torch.cuda.current_stream(dev)
+    m = torch.from_numpy(w.initial_m()).to(device=dev, dtype=tdt).contiguous()
+    flush = torch.empty(int(256 * 2**20) // 4, dtype=torch.float32, device=dev)  # > 2x L2
+
+    def field_step(buf, i):
+        st, _, res = mm.mm_hysteresis_sweep(prob, buf, F[: i + 1], start=i, opts=opts, stream=stream)
+        return st, res[i]
+
+    for i in range(args.warmup):
+        field_step(m, i)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+
+    K = args.steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    evals = launches = 0
+    statuses = []
+    sampler = ClockSampler(local)
+    t_wall = time.perf_counter()
+    with sampler:
+        torch.cuda.synchronize()
+        for j in range(K):
+            i = (args.warmup + j) % len(F)
+            flush.zero_()
+            evs[j][0].record(stream)
+            st, r = field_step(m, i)
+            evs[j][1].record(stream)
+            evals += r.heff_evals
+            launches += r.kernel_launches
+            statuses.append(st)
+        torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if ws > 1:
+        dist.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    clocks = sampler.summary()
+
+    # end to end through the C ABI with the magnetisation in pinned host memory
+    mh = torch.empty(m.shape, dtype=tdt, pin_memory=True)
+    mh.copy_(m.cpu())
+    e2e_evals = 0
+    e2e_ms = 0.0
+    for j in range(K):
+        i = (args.warmup + K + j) % len(F)
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, r = field_step(mh, i)   # host buffer: H2D in, minimise, D2H out inside the call
+        e2e_ms += 1e3 * (time.perf_counter() - t0)
+        e2e_evals += r.heff_evals
+
+    # per-kernel device times for the roofline
+    ktimes = mm.mm_kernel_times(prob, m, F[args.warmup], reps=30, stream=stream)
+    model = algorithmic_model(info, esz)
+
+    tot = torch.tensor([float(evals), ms, float(e2e_evals), e2e_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        s = tot.clone(); dist.all_reduce(s, op=dist.ReduceOp.SUM)
+        mx = tot.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        evals_all, ms_max, e2e_all, e2e_max = s[0].item(), mx[1].item(), s[2].item(), mx[3].item()
+    else:
+        evals_all, ms_max, e2e_all, e2e_max = evals, ms, e2e_evals, e2e_ms
+    if rank != 0:
+        dist.destroy_process_group() if ws > 1 else None
+        return 0
+
+    value = evals_all / (ms_max / 1e3)
+    e2e_value = e2e_all / (e2e_max / 1e3)
+    dom = max(ktimes, key=ktimes.get)
+    peaks = measured_peaks()
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    if prec == mm.MM_FP64:
+        peak = N_SM * FP64_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
+        achieved = model[dom]["flops"] / (ktimes[dom] * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": f"FP64 FMA: {N_SM} SMs x {FP64_FMA_PER_SM_CLK} FMA/clk x 2 flop at {sm_mhz:.0f} MHz"}
+    else:
+        peak = peaks.get("hbm_gbs", 6800.0)
+        achieved = model[dom]["bytes"] / (ktimes[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)" if "hbm_gbs" in peaks else "fallback"}
+    roof["kernel"] = dom
+    roof["traffic"] = load_traffic(dom, w.name, args.precision)
+    roof["hbm_frac_of_measured"] = model[dom]["bytes"] / (ktimes[dom] * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0)
+    roof["stage_ms"] = ktimes
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
+        "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == mm.MM_FP64 else "f32", "data": "synthetic",
+        "config": {"workload": w.name, "cells": [w.nx, w.ny, w.nz], "padded": [info["px"], info["py"], info["pz"]],
+                   "precision": args.precision, "step": "one field value of the 1 mT sweep minimised to tol 1e-5",
+                   "fields_mT": [round(float(F[(args.warmup + j) % len(F)] @ inputs.field_direction(1.0)) * inputs.MU0 * 1e3, 3) for j in range(K)],
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas{ws}"},
+        "evals_per_step": evals / K, "wall_s": t_wall,
+        "loop_time_s_est": (201 * evals / K) / value,
+        "statuses": statuses,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(3 * w.ncells * esz + 24),
+                "d2h_bytes_per_step": int(3 * w.ncells * esz + 64)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "roofline": roof,
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        rate, n_ev, cores, dt = oracle_rate(w)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{n_ev} oracle H_eff+step iterations at {w.name} in {dt:.1f} s"}
+    print(json.dumps(line))
+    prob.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,246 @@
+/*
+ * mm.h -- C ABI of libmmgb.so: energy-minimising hysteresis for
+ * finite-difference micromagnetics on one NVIDIA GB300 (sm_103a).
+ *
+ * The method is the one of Abert, Wautischer, Bruckner, Satz and Suess,
+ * "Efficient Energyminimization in Finite-Difference Micromagnetics:
+ * Speeding up Hysteresis Computations" (arXiv 1405.2728):
+ *   - effective field H_eff = -(1/(mu0 Ms)) dU/dm, Eq. (effective_field), with
+ *     the demagnetisation field as an FFT convolution on a regular cuboid grid
+ *     (Section 3), exchange, uniaxial anisotropy and Zeeman terms (Section 4);
+ *   - projected gradient g = m x (m x H_eff), Eq. (projected_direction) and the
+ *     auxiliary fields of Eq. (stepsize);
+ *   - norm-preserving midpoint step, Eq. (implicit_gradient_descent), solved in
+ *     closed form;
+ *   - Barzilai-Borwein step sizes tau^1, tau^2 of Eq. (stepsize) used
+ *     alternately, a small first step and a sup-norm stop rule (Section 2);
+ *   - the hysteresis driver: one minimisation per field value, warm-started
+ *     from the previous magnetisation (Section 4).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Units: SI.  Lengths in m, Ms and fields in A/m, A in J/m, K in J/m^3,
+ *   energies in J.  mu0 = 4 pi 1e-7 exactly.
+ * Layout: a vector field is structure-of-arrays [3][nz][ny][nx] (component,
+ *   then z, y, x with x fastest), contiguous, N = nx*ny*nz cells per component.
+ *   Scalars per cell are [nz][ny][nx].
+ * Element type: double for MM_FP64 problems, float for MM_FP32 problems.
+ * Pointers marked "host or device" may be either: the library asks the CUDA
+ *   runtime which one it is.  Device pointers are used in place; host
+ *   memory (preferably pinned) is staged through library-owned device buffers
+ *   inside the call.  Device pointers must be 16-byte aligned.
+ * Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *   All device work of a call is issued on it.  Calls that return host
+ *   results synchronise that stream before returning; mm_heff with device
+ *   pointers returns without synchronising.
+ * Ownership: the caller owns every m, H and K/u buffer it passes; the library
+ *   keeps no reference to them after the call returns.  The library owns the
+ *   problem object and everything in it (tensor spectra, FFT twiddles,
+ *   workspaces, CUDA graphs), released by mm_destroy.
+ * Errors: every call returns an mm_status code and never aborts the process.
+ *   On MM_ERR_ARG / MM_ERR_UNSUPPORTED nothing is written.  MM_ERR_CUDA
+ *   means a CUDA runtime call failed (mm_last_cuda_error tells which); the
+ *   problem should then be destroyed.
+ * Threading: a problem object must not be used by two host threads at once.
+ */
+#ifndef MMGB_MM_H
+#define MMGB_MM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define MM_API __attribute__((visibility("default")))
+#else
+#define MM_API
+#endif
+
+typedef struct mm_problem mm_problem; /* opaque, owned by the library */
+
+typedef enum {
+    MM_OK = 0,
+    MM_ERR_ARG = -1,            /* invalid argument (null, non-positive size, non-unit axis, misaligned) */
+    MM_ERR_OOM = -2,            /* device allocation failed */
+    MM_ERR_CUDA = -3,           /* a CUDA runtime call failed */
+    MM_ERR_NOT_CONVERGED = -4,  /* max_iter steps taken without meeting tol; m holds the last iterate */
+    MM_ERR_NONFINITE = -5,      /* a non-finite torque, energy or step size appeared */
+    MM_ERR_TIMEOUT = -6,        /* the minimiser's wall-clock limit (timeout_s) passed; m holds the last iterate */
+    MM_ERR_UNSUPPORTED = -7     /* valid but outside what this build supports (see mm_setup_geometry) */
+} mm_status;
+
+enum { MM_FP64 = 0, MM_FP32 = 1 };                   /* element type and arithmetic of the field path */
+enum { MM_STEP_CAYLEY = 0, MM_STEP_NORMALIZE = 1 };  /* update rule, see mm_min_opts */
+
+/* Regular cuboid grid of nx*ny*nz cells of size dx*dy*dz (Section 3). */
+typedef struct {
+    int nx, ny, nz;
+    double dx, dy, dz;
+} mm_grid;
+
+/* Material (Section 4): saturation magnetisation Ms > 0, exchange A >= 0,
+ * uniaxial anisotropy K (any sign) with unit easy axis u.  Optional per-cell
+ * overrides (host or device, double, read once by mm_setup_geometry):
+ * K_cell [nz][ny][nx] replaces K; u_cell [3][nz][ny][nx] replaces u and must
+ * hold unit vectors. */
+typedef struct {
+    double Ms, A, K;
+    double u[3];
+    const double *K_cell;
+    const double *u_cell;
+} mm_material;
+
+/*
+ * mm_newell -- the cell-averaged demagnetisation tensor of the grid (the
+ * convolution kernel of the FFT demagnetisation field, Section 3; Newell,
+ * Williams and Dunlop, J. Geophys. Res. 98 (1993) 9551), computed on the GPU
+ * in double-double arithmetic and rounded to double.
+ *
+ * N_out (host or device, double): [6][nz][ny][nx], components xx, yy, zz, xy,
+ * xz, yz at the non-negative offsets (i, j, k) cells, 0 <= i < nx etc.
+ * Other offsets follow by symmetry: N_aa is even in every coordinate, N_ab is
+ * odd in coordinate a and in coordinate b.  With this tensor the
+ * demagnetisation field is H_d(r_i) = -Ms sum_j N(r_i - r_j) m_j.
+ * Returns MM_OK, MM_ERR_ARG, MM_ERR_OOM or MM_ERR_CUDA; synchronises `stream`.
+ */
+MM_API int mm_newell(const mm_grid *grid, double *N_out, void *stream);
+
+/*
+ * mm_setup_geometry -- create a problem: validates the grid and material,
+ * allocates device workspaces, computes the Newell tensor (as mm_newell), its
+ * Fourier spectrum on the zero-padded grid (padded size per axis: the smallest
+ * power of two >= 2n-1, and >= 2 along x), and captures the minimiser's CUDA
+ * graph.  precision = MM_FP64 or MM_FP32: element type of m/H and of the FFT
+ * and stencil arithmetic; reductions (step sizes, energies, averages) are
+ * always accumulated in double.
+ * Supported in this build (else MM_ERR_UNSUPPORTED): nx <= 2048 (padded x
+ * length <= 4096), nz <= 4 (padded z length <= 8), nz * Py <= 2048, and the
+ * padded y-z plane of one x-frequency, 3 * nz * (Py + 1) complex values,
+ * within 200 KiB of shared memory -- thin films such as 512 x 256 x 4 (FP64)
+ * or 1024 x 512 x 4 (FP32).
+ * On success *out receives the new problem.  Synchronises `stream`.
+ */
+MM_API int mm_setup_geometry(const mm_grid *grid, const mm_material *mat, int precision, void *stream,
+                      mm_problem **out);
+
+/* mm_destroy -- free a problem and everything it owns (NULL is accepted). */
+MM_API int mm_destroy(mm_problem *prob);
+
+/*
+ * mm_heff -- effective field, Eq. (effective_field) (Sections 3 and 4):
+ *   H = H_demag + H_exchange + H_anisotropy + H_ext, with
+ *   H_demag,i    = -Ms sum_j N(r_i - r_j) m_j        (zero-padded FFT convolution)
+ *   H_exchange,i = (2A/(mu0 Ms)) sum_{j in nb(i)} (m_j - m_i)/d_ij^2   (six
+ *                  neighbours; neighbours outside the grid are absent)
+ *   H_aniso,i    = (2K_i/(mu0 Ms)) (m_i . u_i) u_i
+ * m (host or device) [3][nz][ny][nx] unit vectors; Hext[3] (host, A/m);
+ * H_out (host or device) [3][nz][ny][nx] in A/m.
+ */
+MM_API int mm_heff(mm_problem *prob, const void *m, const double Hext[3], void *H_out, void *stream);
+
+/*
+ * mm_energy -- the discrete energy whose cell gradient is mm_heff:
+ *   E_demag = -(mu0 Ms V/2) sum m.H_demag, E_exchange = A V sum_{neighbour
+ *   pairs} |m_j - m_i|^2/d^2, E_aniso = sum K_i V (1 - (m_i.u_i)^2),
+ *   E_zeeman = -mu0 Ms V sum m.H_ext, with V = dx dy dz.
+ * E_out (host) [5] = demag, exchange, anisotropy, Zeeman, total, in J.
+ * Synchronises `stream`.
+ */
+MM_API int mm_energy(mm_problem *prob, const void *m, const double Hext[3], double E_out[5], void *stream);
+
+/* Options of one minimisation (Section 2).
+ * tol       stop when max_i |m_i x H_i| / Ms < tol (the sup-norm stop rule,
+ *           evaluated on m_k before stepping).
+ * tau0      first step size (the "reasonably small guess"), in m/A; <= 0
+ *           selects 1e-2/Ms.
+ * max_iter  at most this many steps (so at most max_iter+1 field evaluations).
+ * step_kind MM_STEP_CAYLEY: the midpoint scheme, Eq. (implicit_gradient_descent),
+ *           in closed form m' = [(1 - tau^2|g|^2/4) m - tau g]/(1 + tau^2|g|^2/4);
+ *           MM_STEP_NORMALIZE: m' = (m - tau g)/|m - tau g|, the explicit
+ *           projected step Eq. (projected_gradient_descent) renormalised.
+ * timeout_s wall-clock limit of the device loop in seconds (<= 0: none).
+ * Step sizes: tau_0 = tau0; for k >= 1, with s = m_k - m_{k-1} and
+ * y = g_k - g_{k-1} summed over all cells, tau^1 = s.s/s.y on odd k and
+ * tau^2 = s.y/y.y on even k (Eq. stepsize, alternating); when that quotient
+ * is not finite and positive, sqrt(s.s/y.y), else tau0. */
+typedef struct {
+    double tol;
+    double tau0;
+    long max_iter;
+    int step_kind;
+    double timeout_s;
+} mm_min_opts;
+
+/* Outcome of one minimisation. */
+typedef struct {
+    long iters;          /* steps taken */
+    long heff_evals;     /* effective-field evaluations (iters + 1) */
+    double max_torque;   /* max_i |m_i x H_i| / Ms at the returned m */
+    double energy;       /* total energy at the returned m, J */
+    int converged;       /* 1 if max_torque < tol */
+    int status;          /* mm_status of this minimisation */
+    long kernel_launches;/* CUDA kernels this minimisation launched */
+} mm_min_result;
+
+/*
+ * mm_minimize -- minimise the energy at fixed external field Hext (host, A/m)
+ * starting from m (host or device, in/out, unit vectors), following Section 2.
+ * The loop runs on the device (a CUDA graph with a device-side conditional
+ * loop); the host waits once at the end.  res (host, nullable) receives the
+ * outcome.  Returns MM_OK, MM_ERR_NOT_CONVERGED, MM_ERR_NONFINITE,
+ * MM_ERR_TIMEOUT (m then holds the last iterate), MM_ERR_ARG or MM_ERR_CUDA.
+ * Synchronises `stream`.
+ */
+MM_API int mm_minimize(mm_problem *prob, void *m, const double Hext[3], const mm_min_opts *opts,
+                mm_min_result *res, void *stream);
+
+/*
+ * mm_hysteresis_sweep -- the hysteresis driver of Section 4: for field values
+ * H_list[start..n-1] (host, [n][3], A/m) in order, minimise as mm_minimize
+ * starting from the previous result (the step-size history restarts at every
+ * field value) and record the average magnetisation <m> = (1/N) sum_i m_i in
+ * mavg (host, [n][3]; entries before `start` untouched).  m (host or device,
+ * in/out) holds the start state and receives the final state.  per_step
+ * (host, nullable, [n]) receives each field value's outcome.  The whole sweep
+ * is issued without host round trips; the host synchronises once at the end.
+ * Returns MM_OK if every field value converged, else the first non-OK status
+ * met (the sweep still runs to the end).  `start` allows resuming a sweep.
+ */
+MM_API int mm_hysteresis_sweep(mm_problem *prob, void *m, const double *H_list, int n, int start,
+                        const mm_min_opts *opts, double *mavg, mm_min_result *per_step,
+                        void *stream);
+
+/* Sizes of a problem, for reporting and for callers that size buffers. */
+typedef struct {
+    int nx, ny, nz;
+    int px, py, pz;            /* zero-padded FFT grid */
+    int precision;
+    long cells;
+    long workspace_bytes;      /* device memory owned by the problem */
+    long spectrum_bytes;       /* one padded field spectrum (3 components, x-half) */
+    long tensor_bytes;         /* stored tensor spectra */
+} mm_info;
+MM_API int mm_problem_info(const mm_problem *prob, mm_info *info);
+
+/*
+ * mm_kernel_times -- instrumentation: evaluate H_eff plus one minimiser step
+ * `reps` times on `stream` with CUDA events around each kernel, and report the
+ * average device time of each kernel stage in ms.  names[i] are static
+ * strings.  Used by the benchmark to turn algorithmic bytes/flops into
+ * achieved rates.  *count (in: capacity of the arrays; out: stages written).
+ * Leaves the problem's minimiser state undefined; synchronises `stream`.
+ */
+MM_API int mm_kernel_times(mm_problem *prob, const void *m, const double Hext[3], int reps, double *ms_out,
+                    const char **names, int *count, void *stream);
+
+/* Human-readable text of a status code (static string). */
+MM_API const char *mm_status_string(int status);
+
+/* Text of the last CUDA error seen by this thread inside the library (static). */
+MM_API const char *mm_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MMGB_MM_H */

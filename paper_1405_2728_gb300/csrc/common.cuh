@@ -1,0 +1,170 @@
+// Shared device/host definitions of libmmgb: complex helpers, kernel
+// parameter blocks, the device-resident minimiser state and the host-side
+// problem object.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mm.h"
+
+#define MM_MU0 (4e-7 * 3.14159265358979323846)
+
+// ---------------------------------------------------------------------------
+// complex values: double2 / float2 (re = x, im = y)
+// ---------------------------------------------------------------------------
+template <typename T> struct cvec;
+template <> struct cvec<double> { typedef double2 type; };
+template <> struct cvec<float> { typedef float2 type; };
+
+template <typename V> __device__ __forceinline__ V cmake(decltype(V().x) a, decltype(V().x) b) { V r; r.x = a; r.y = b; return r; }
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { V r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { V r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) { V r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r; }
+// a * conj(b)
+template <typename V> __device__ __forceinline__ V cmulc(V a, V b) { V r; r.x = a.x * b.x + a.y * b.y; r.y = a.y * b.x - a.x * b.y; return r; }
+template <typename V> __device__ __forceinline__ V cconj(V a) { V r; r.x = a.x; r.y = -a.y; return r; }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV, typename V> __device__ __forceinline__ V cmul_mi(V a)
+{
+    V r;
+    if (INV) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// minimiser state, resident in device memory (one per problem)
+// ---------------------------------------------------------------------------
+enum { MMS_RUNNING = 0, MMS_CONVERGED = 1, MMS_MAXITER = 2, MMS_NONFINITE = 3, MMS_TIMEOUT = 4 };
+
+// Reduction slots written per CTA by the local-terms kernel (double each).
+enum {
+    RED_SS = 0,      // sum s.s   (s = m_k - m_{k-1})
+    RED_SY,          // sum s.y   (y = g_k - g_{k-1})
+    RED_YY,          // sum y.y
+    RED_T2MAX,       // max |m x H|^2
+    RED_ED,          // sum m.H_demag
+    RED_EEX,         // sum m.H_exchange
+    RED_EAN,         // sum K (1 - (m.u)^2)
+    RED_EZ,          // sum m.H_ext
+    RED_MX, RED_MY, RED_MZ,  // sum m
+    RED_NSLOT
+};
+
+struct MinState {
+    // control, written by the host-side init kernel
+    double tau0, tol_abs;     // tol_abs = tol * Ms (compared with |m x H|)
+    double Hext[3];
+    long max_iter;
+    int step_kind;
+    int base;                 // m buffer holding iterate 0
+    unsigned long long t_start_ns, timeout_ns;
+    // evolving
+    long k;                   // current iterate index (evaluations so far - 1 once evaluated)
+    double tau;               // step size for the next update
+    int status;               // MMS_*
+    long evals;
+    double max_torque;        // max |m x H| / Ms at iterate k
+    double energy[5];         // demag, exchange, anisotropy, zeeman, total (J) at iterate k
+    double mavg[3];
+    long launches;            // kernels launched by the loop body so far
+};
+
+// Per-step record of a sweep
+struct StepRecord {
+    double mavg[3];
+    double max_torque, energy;
+    long iters, evals, launches;
+    int status;
+};
+
+// ---------------------------------------------------------------------------
+// Geometry shared by the field kernels (passed by value)
+// ---------------------------------------------------------------------------
+struct Geom {
+    int nx, ny, nz;
+    int Px, Py, Pz;        // padded FFT lengths
+    int Hx, C;             // Hx = Px/2 (packed complex length), C = Hx + 1 x-frequencies
+    int lhx, lpy;          // log2(Hx), log2(Py)
+    int Gx, Gy;            // threads per FFT row: max(1, L/8)
+    int TY;                // y rows per CTA in the x kernels
+    int rsx, rsy;          // smem row strides (complex elements) of the x and y FFT rows
+    long N;                // cells
+    double dx, dy, dz;
+    double Ms;
+    double cex_x, cex_y, cex_z;   // 2A/(mu0 Ms d^2) per axis
+    double can;                    // 2/(mu0 Ms) (times K per cell)
+    double K;                      // uniform K
+    double u[3];                   // uniform axis
+};
+
+// Field evaluation modes of the x-inverse/local kernel
+enum { MODE_HEFF = 0, MODE_ENERGY = 1, MODE_MIN = 2 };
+
+template <typename T>
+struct FieldPtrs {
+    typedef typename cvec<T>::type V;
+    const T *m_src;        // field input for MODE_HEFF/ENERGY, or NULL (then mbuf by state)
+    T *H_out;              // MODE_HEFF output
+    T *mbuf[2];            // minimiser iterate buffers
+    T *gbuf[2];            // projected-gradient buffers
+    V *W;                  // spectrum [C][3][nz][ny]
+    const T *Nhat;         // tensor spectra [C][Pz/2+1][Py/2+1][6], scaled by -Ms/(Px Py Pz)
+    const V *tw_px;        // exp(-2 pi i t/Px), t < Px
+    const V *tw_py;        // exp(-2 pi i t/Py), t < Py
+    const V *tw_pz;        // exp(-2 pi i t/Pz), t < Pz
+    const T *Kc;           // per-cell K or NULL
+    const T *uc;           // per-cell axis [3][N] or NULL
+    double *partials;      // [nblocks][RED_NSLOT]
+    MinState *st;          // minimiser state (MODE_MIN and updates)
+    const double *Hext;    // device copy of H_ext for MODE_HEFF/ENERGY (or st->Hext)
+};
+
+// ---------------------------------------------------------------------------
+// host-side problem object
+// ---------------------------------------------------------------------------
+struct mm_problem {
+    mm_grid grid;
+    mm_material mat;
+    int precision;
+    Geom g;
+    size_t esz;            // sizeof(T)
+    // device memory
+    void *mbuf[2], *gbuf[2];
+    void *W;
+    void *Nhat;
+    void *tw_px, *tw_py, *tw_pz;
+    void *Kc, *uc;
+    double *partials;
+    int nblk_x;            // CTAs of the x kernels (= partial slots)
+    MinState *st;
+    MinState *st_host;     // pinned mirror
+    double *Hext_dev;
+    void *stage_in, *stage_out;    // staging for host m / H
+    StepRecord *rec_dev;   // sweep records (capacity rec_cap)
+    int rec_cap;
+    long bytes;
+    // graph of the device-side minimiser loop
+    cudaGraph_t graph;
+    cudaGraphExec_t gexec;
+    cudaGraphConditionalHandle cond;
+    int graph_ready;
+    int dev;
+};
+
+// launchers implemented in heff.cu
+int mm_launch_min_body(mm_problem *p, cudaGraphConditionalHandle h, cudaStream_t s, int use_cond);
+int mm_kernel_stage_times(mm_problem *p, int reps, double *ms, const char **names, int *count, cudaStream_t s);
+int mm_launch_init_state(mm_problem *p, const double Hext[3], const mm_min_opts *o, int reset_base, cudaStream_t s);
+int mm_launch_record(mm_problem *p, int step, cudaStream_t s);
+int mm_launch_copy_result(mm_problem *p, void *dst, cudaStream_t s);
+size_t mm_smem_x(const mm_problem *p);
+size_t mm_smem_yz(const mm_problem *p);
+int mm_heff_configure(mm_problem *p);
+int mm_launch_twiddles(mm_problem *p, cudaStream_t s);
+// implemented in newell.cu
+int mm_newell_device(const mm_grid *g, double *N_dev, cudaStream_t s);
+int mm_tensor_spectrum(mm_problem *p, const double *N_dev, cudaStream_t s);
+
+// error bookkeeping (api.cu)
+void mm_set_cuda_error(cudaError_t e, const char *where);

@@ -1,0 +1,202 @@
+// Shared-memory FFT building blocks for the zero-padded demagnetisation
+// convolution (the "FFT accelerated convolution" of Section 3).
+//
+// A row of L = 2^l complex values lives in shared memory and is transformed
+// in place by G = max(1, L/8) threads with self-sorting Stockham passes
+// (Stockham; Cochran et al., Proc. IEEE 55 (1967) 1664): an optional first
+// pass of radix 2 or 4 and then radix-8 passes.  Each thread keeps one radix-8
+// butterfly (or two radix-4 / four radix-2 ones) in registers per pass; a
+// barrier separates the loads of a pass from its stores, which makes the
+// in-place update safe.  Twiddles come from a table tw[t] = exp(-2 pi i t/L')
+// read with stride ts = L'/L.
+//
+// Zero padding is exploited where the convolution needs it:
+//  HALF_IN : the upper half of the input is known to be zero, so the first
+//            pass reads half of its inputs and skips the arithmetic on zeros;
+//  HALF_OUT: only the lower half of the output is wanted, so the last pass
+//            computes and stores only those values.
+#pragma once
+
+#include "common.cuh"
+
+template <typename V> __device__ __forceinline__ V czero() { V r; r.x = 0; r.y = 0; return r; }
+
+// 2-point DFT
+template <bool HIN, typename V> __device__ __forceinline__ void dft2(V &a0, V &a1)
+{
+    if (HIN) { a1 = a0; return; }
+    V t = a0;
+    a0 = cadd(t, a1);
+    a1 = csub(t, a1);
+}
+
+// 4-point DFT, forward uses -i, inverse +i; outputs in natural order
+template <bool INV, bool HIN, typename V> __device__ __forceinline__ void dft4(V &x0, V &x1, V &x2, V &x3)
+{
+    V t0, t1, t2, t3;
+    if (HIN) {           // x2 = x3 = 0
+        t0 = x0; t1 = x0; t2 = x1; t3 = cmul_mi<INV>(x1);
+    } else {
+        t0 = cadd(x0, x2); t1 = csub(x0, x2);
+        t2 = cadd(x1, x3); t3 = cmul_mi<INV>(csub(x1, x3));
+    }
+    x0 = cadd(t0, t2);
+    x2 = csub(t0, t2);
+    x1 = cadd(t1, t3);
+    x3 = csub(t1, t3);
+}
+
+// 8-point DFT by one radix-2 decimation-in-frequency split into two 4-point
+// DFTs: u_n = a_n + a_{n+4}, v_n = (a_n - a_{n+4}) W^n, X_{2k} = DFT4(u)_k,
+// X_{2k+1} = DFT4(v)_k, W = exp(-+ i pi/4).
+template <bool INV, bool HIN, typename V> __device__ __forceinline__ void dft8(V *a)
+{
+    typedef decltype(a[0].x) T;
+    const T r = (T)0.70710678118654752440084436210484903928;
+    V u0, u1, u2, u3, d0, d1, d2, d3;
+    if (HIN) {
+        u0 = a[0]; u1 = a[1]; u2 = a[2]; u3 = a[3];
+        d0 = a[0]; d1 = a[1]; d2 = a[2]; d3 = a[3];
+    } else {
+        u0 = cadd(a[0], a[4]); d0 = csub(a[0], a[4]);
+        u1 = cadd(a[1], a[5]); d1 = csub(a[1], a[5]);
+        u2 = cadd(a[2], a[6]); d2 = csub(a[2], a[6]);
+        u3 = cadd(a[3], a[7]); d3 = csub(a[3], a[7]);
+    }
+    V v1, v2, v3;
+    if (INV) {
+        v1.x = r * (d1.x - d1.y); v1.y = r * (d1.x + d1.y);
+        v2.x = -d2.y;             v2.y = d2.x;
+        v3.x = -r * (d3.x + d3.y); v3.y = r * (d3.x - d3.y);
+    } else {
+        v1.x = r * (d1.x + d1.y); v1.y = r * (d1.y - d1.x);
+        v2.x = d2.y;              v2.y = -d2.x;
+        v3.x = r * (d3.y - d3.x); v3.y = -r * (d3.x + d3.y);
+    }
+    dft4<INV, false>(u0, u1, u2, u3);
+    dft4<INV, false>(d0, v1, v2, v3);
+    a[0] = u0; a[1] = d0; a[2] = u1; a[3] = v1;
+    a[4] = u2; a[5] = v2; a[6] = u3; a[7] = v3;
+}
+
+template <int R, bool INV, bool HIN, typename V> __device__ __forceinline__ void dftR(V *a)
+{
+    if (R == 2) dft2<HIN>(a[0], a[1]);
+    else if (R == 4) dft4<INV, HIN>(a[0], a[1], a[2], a[3]);
+    else dft8<INV, HIN>(a);
+}
+
+// One Stockham pass of radix R over a row of length L (Ns = product of the
+// radices of the previous passes).  Thread j handles butterflies j + q G,
+// q < 8/R.  Caller guarantees visibility of the row before the call; the
+// pass ends with a barrier.
+template <int R, bool INV, bool HIN, bool HOUT, typename V>
+__device__ __forceinline__ void stockham_pass(V *row, int L, int Ns, int j, int G,
+                                              const V *__restrict__ tw, int ts, bool active)
+{
+    constexpr int NB = 8 / R;
+    V v[8];
+    const int LR = L / R;
+#pragma unroll
+    for (int q = 0; q < NB && active; ++q) {
+        const int b = j + q * G;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            v[q * R + r] = (HIN && r >= R / 2) ? czero<V>() : row[b + r * LR];
+        if (Ns > 1) {
+            const int k = b & (Ns - 1);
+            const int step = (L / (Ns * R)) * k * ts;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const V w = tw[r * step];
+                v[q * R + r] = INV ? cmulc(v[q * R + r], w) : cmul(v[q * R + r], w);
+            }
+        }
+        dftR<R, INV, HIN>(&v[q * R]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NB && active; ++q) {
+        const int b = j + q * G;
+        const int k = b & (Ns - 1);
+        const int base = (b - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < (HOUT ? R / 2 : R); ++r) row[base + r * Ns] = v[q * R + r];
+    }
+    __syncthreads();
+}
+
+// In-place FFT of one shared-memory row of length L = 2^logL (forward:
+// exp(-i...), inverse: exp(+i...), unnormalised).  Every thread of the CTA
+// must call this with the same L (it contains barriers); thread j in [0, G)
+// of the row's group works on it.  Threads with active == false (padding
+// threads of the CTA) only take part in the barriers.  The caller
+// synchronises before the call so that the row's contents are visible; the
+// row is final after return.
+template <bool INV, bool HIN, bool HOUT, typename V>
+__device__ void fft_row(V *row, int L, int logL, int j, const V *__restrict__ tw, int ts, bool active)
+{
+    if (L == 1) return;
+    if (L < 8) {
+        // G == 1: the single thread of the row does the whole transform.  The
+        // barriers stay outside the branches so that every thread of a warp
+        // executes the same barrier instruction.
+        V a[4];
+        if (active) {
+            a[0] = row[0];
+            a[1] = (HIN && L == 2) ? czero<V>() : row[1];
+            if (L == 2) {
+                dft2<HIN>(a[0], a[1]);
+            } else {
+                a[2] = HIN ? czero<V>() : row[2];
+                a[3] = HIN ? czero<V>() : row[3];
+                dft4<INV, HIN>(a[0], a[1], a[2], a[3]);
+            }
+        }
+        __syncthreads();
+        if (active) {
+            row[0] = a[0];
+            if (L == 2) {
+                if (!HOUT) row[1] = a[1];
+            } else {
+                row[1] = a[1];
+                if (!HOUT) { row[2] = a[2]; row[3] = a[3]; }
+            }
+        }
+        __syncthreads();
+        return;
+    }
+    const int G = L >> 3;
+    const int rem = logL % 3;
+    const int n8 = logL / 3;
+    int Ns = 1;
+    bool first = true;
+    if (rem == 1) {
+        stockham_pass<2, INV, HIN, false>(row, L, Ns, j, G, tw, ts, active);
+        Ns = 2; first = false;
+    } else if (rem == 2) {
+        stockham_pass<4, INV, HIN, false>(row, L, Ns, j, G, tw, ts, active);
+        Ns = 4; first = false;
+    }
+    for (int p = 0; p < n8; ++p) {
+        const bool last = (p == n8 - 1);
+        if (first && HIN) {
+            if (last && HOUT) stockham_pass<8, INV, true, true>(row, L, Ns, j, G, tw, ts, active);
+            else stockham_pass<8, INV, true, false>(row, L, Ns, j, G, tw, ts, active);
+        } else {
+            if (last && HOUT) stockham_pass<8, INV, false, true>(row, L, Ns, j, G, tw, ts, active);
+            else stockham_pass<8, INV, false, false>(row, L, Ns, j, G, tw, ts, active);
+        }
+        Ns <<= 3;
+        first = false;
+    }
+}
+
+// Small in-register DFT of length PZ (1, 2, 4 or 8) for the z direction,
+// with the same half-input / half-output pruning flags.
+template <int PZ, bool INV, bool HIN, typename V> __device__ __forceinline__ void dft_small(V *a)
+{
+    if (PZ == 2) dft2<HIN>(a[0], a[1]);
+    else if (PZ == 4) dft4<INV, HIN>(a[0], a[1], a[2], a[3]);
+    else if (PZ == 8) dft8<INV, HIN>(a);
+}

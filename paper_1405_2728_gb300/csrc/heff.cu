@@ -1,0 +1,735 @@
+// Effective-field and minimiser-step kernels (sm_103a).
+//
+// One evaluation of H_eff (Eq. effective_field; Sections 3 and 4) is three
+// kernels over the zero-padded grid, and the minimiser (Section 2) adds a
+// one-CTA reduction kernel:
+//
+//  k_xfwd     per (z, tile of TY rows): optional minimiser step (the closed
+//             form of the midpoint scheme, Eq. implicit_gradient_descent, or
+//             the renormalised explicit step) fused with the real-to-complex
+//             FFT along x of the three components, zero padding nx -> Px,
+//             written transposed to the spectrum W[kx][c][z][y].
+//  k_yz       per x-frequency kx: FFT along y (padding ny -> Py) in shared
+//             memory, then per ky in registers FFT along z, the product with
+//             the symmetric 3x3 tensor spectrum (H^ = -Ms N^ m^, normalisation
+//             folded into N^), inverse FFT along z, inverse FFT along y keeping
+//             the first ny rows.
+//  k_xinv     per (z, tile): complex-to-real inverse FFT along x keeping nx
+//             values, then the local terms: exchange (six-point stencil, free
+//             faces), uniaxial anisotropy, Zeeman.  Depending on the mode it
+//             writes H, or accumulates energies, or forms the projected
+//             gradient g = m x (m x H) (Eq. projected_direction) with the
+//             Barzilai-Borwein sums s.s, s.y, y.y (Eq. stepsize), max |m x H|,
+//             energies and sum m, in double, one partial set per CTA.
+//  k_reduce   one CTA: fixed-order sum of the partials, step size tau^1 / tau^2
+//             alternating (Eq. stepsize), stop rule, and the device-side loop
+//             condition of the CUDA graph.
+#include <cstdio>
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace {
+
+template <typename T> __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
+
+// ---------------------------------------------------------------------------
+// k_xfwd
+// ---------------------------------------------------------------------------
+template <typename T, bool MIN>
+__global__ void __launch_bounds__(768) k_xfwd(Geom g, FieldPtrs<T> P)
+{
+    typedef typename cvec<T>::type V;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *S = reinterpret_cast<V *>(smem_raw);
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int TY = g.TY, y0 = blockIdx.x * TY, z = blockIdx.y;
+    const int nx = g.nx, ny = g.ny, Px = g.Px;
+    const long N = g.N;
+
+    const T *src;
+    T *dst = nullptr;
+    const T *gp = nullptr;
+    T tau = 0;
+    int step_kind = 0;
+    if (MIN) {
+        const MinState *st = P.st;
+        const long k = st->k;
+        const int cur = st->base ^ (int)(k & 1);
+        if (k > 0) {
+            src = P.mbuf[cur ^ 1];
+            dst = P.mbuf[cur];
+            gp = P.gbuf[(int)((k - 1) & 1)];
+            tau = (T)st->tau;
+            step_kind = st->step_kind;
+        } else {
+            src = P.mbuf[cur];
+        }
+    } else {
+        src = P.m_src;
+    }
+
+    // load (and step) the tile, write reals into the rows: row (c, yl) holds Px reals
+    for (int e = tid; e < TY * nx; e += nth) {
+        const int yl = e / nx, x = e - yl * nx, y = y0 + yl;
+        T m0 = 0, m1 = 0, m2 = 0;
+        if (y < ny) {
+            const long n = ((long)z * ny + y) * nx + x;
+            m0 = src[n]; m1 = src[N + n]; m2 = src[2 * N + n];
+            if (MIN && dst) {
+                const T g0 = gp[n], g1 = gp[N + n], g2 = gp[2 * N + n];
+                if (step_kind == MM_STEP_CAYLEY) {
+                    const T q = (T)0.25 * tau * tau * (g0 * g0 + g1 * g1 + g2 * g2);
+                    const T a = (T)1 - q, inv = (T)1 / ((T)1 + q);
+                    m0 = (a * m0 - tau * g0) * inv;
+                    m1 = (a * m1 - tau * g1) * inv;
+                    m2 = (a * m2 - tau * g2) * inv;
+                } else {
+                    m0 -= tau * g0; m1 -= tau * g1; m2 -= tau * g2;
+                    const T inv = (T)1 / sqrt(m0 * m0 + m1 * m1 + m2 * m2);
+                    m0 *= inv; m1 *= inv; m2 *= inv;
+                }
+                dst[n] = m0; dst[N + n] = m1; dst[2 * N + n] = m2;
+            }
+        }
+        T *r0 = reinterpret_cast<T *>(S + (0 * TY + yl) * g.rsx);
+        T *r1 = reinterpret_cast<T *>(S + (1 * TY + yl) * g.rsx);
+        T *r2 = reinterpret_cast<T *>(S + (2 * TY + yl) * g.rsx);
+        r0[x] = m0; r1[x] = m1; r2[x] = m2;
+    }
+    const int npad = Px - nx;
+    for (int e = tid; e < 3 * TY * npad; e += nth) {
+        const int row = e / npad, x = nx + (e - row * npad);
+        reinterpret_cast<T *>(S + row * g.rsx)[x] = 0;
+    }
+    __syncthreads();
+
+    // complex FFT of length Hx of the packed rows (upper half zero)
+    {
+        const int row = tid / g.Gx, j = tid - row * g.Gx;
+        const bool act = row < 3 * TY;
+        fft_row<false, true, false>(S + (act ? row : 0) * g.rsx, g.Hx, g.lhx, j, P.tw_px, 2, act);
+    }
+
+    // unpack to the real-input spectrum X[k], k = 0..Hx, and store transposed
+    const int Hx = g.Hx, C = g.C;
+    for (int e = tid; e < TY * 3 * C; e += nth) {
+        const int yl = e % TY, rest = e / TY, c = rest % 3, k = rest / 3;
+        const int y = y0 + yl;
+        const V *row = S + (c * TY + yl) * g.rsx;
+        const V Zk = row[k == Hx ? 0 : k];
+        const V Zm = cconj(row[k == 0 ? 0 : Hx - k]);
+        const V w = P.tw_px[k];
+        const V sum = cadd(Zk, Zm), dif = csub(Zk, Zm);
+        // X = (sum - i w dif) / 2
+        const V wd = cmul(w, dif);
+        V X;
+        X.x = (T)0.5 * (sum.x + wd.y);
+        X.y = (T)0.5 * (sum.y - wd.x);
+        if (y < ny) P.W[(((long)k * 3 + c) * g.nz + z) * ny + y] = X;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_yz
+// ---------------------------------------------------------------------------
+template <typename T, int PZ>
+__global__ void __launch_bounds__(768) k_yz(Geom g, FieldPtrs<T> P)
+{
+    typedef typename cvec<T>::type V;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *S = reinterpret_cast<V *>(smem_raw);
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int kx = blockIdx.x;
+    const int ny = g.ny, nz = g.nz, Py = g.Py;
+    const int nrow = 3 * nz;
+    V *Wk = P.W + (long)kx * nrow * ny;
+
+    for (int e = tid; e < nrow * ny; e += nth) {
+        const int row = e / ny, y = e - row * ny;
+        S[row * g.rsy + y] = Wk[e];
+    }
+    const int npad = Py - ny;
+    for (int e = tid; e < nrow * npad; e += nth) {
+        const int row = e / npad, y = ny + (e - row * npad);
+        S[row * g.rsy + y] = czero<V>();
+    }
+    __syncthreads();
+    const int row = tid / g.Gy, j = tid - row * g.Gy;
+    const bool act = row < nrow;
+    V *myrow = S + (act ? row : 0) * g.rsy;
+    fft_row<false, true, false>(myrow, Py, g.lpy, j, P.tw_py, 1, act);
+
+    // per ky: z transform, tensor product, inverse z transform
+    const int hy = Py / 2, hz = PZ / 2;
+    const T *Nk = P.Nhat + (long)kx * (hz + 1) * (hy + 1) * 6;
+    for (int ky = tid; ky < Py; ky += nth) {
+        V a[3][PZ];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+            for (int zz = 0; zz < PZ; ++zz)
+                a[c][zz] = (zz < nz) ? S[(c * nz + zz) * g.rsy + ky] : czero<V>();
+            if (PZ > 1) dft_small<PZ, false, true>(a[c]);
+        }
+        const int kyr = ky <= hy ? ky : Py - ky;
+        const T sy = ky <= hy ? (T)1 : (T)-1;
+#pragma unroll
+        for (int kz = 0; kz < PZ; ++kz) {
+            const int kzr = kz <= hz ? kz : PZ - kz;
+            const T sz = kz <= hz ? (T)1 : (T)-1;
+            const T *n6 = Nk + ((long)kzr * (hy + 1) + kyr) * 6;
+            const T nxx = ldg(n6 + 0), nyy = ldg(n6 + 1), nzz = ldg(n6 + 2);
+            const T nxy = sy * ldg(n6 + 3), nxz = sz * ldg(n6 + 4), nyz = sy * sz * ldg(n6 + 5);
+            const V m0 = a[0][kz], m1 = a[1][kz], m2 = a[2][kz];
+            V h0, h1, h2;
+            h0.x = nxx * m0.x + nxy * m1.x + nxz * m2.x; h0.y = nxx * m0.y + nxy * m1.y + nxz * m2.y;
+            h1.x = nxy * m0.x + nyy * m1.x + nyz * m2.x; h1.y = nxy * m0.y + nyy * m1.y + nyz * m2.y;
+            h2.x = nxz * m0.x + nyz * m1.x + nzz * m2.x; h2.y = nxz * m0.y + nyz * m1.y + nzz * m2.y;
+            a[0][kz] = h0; a[1][kz] = h1; a[2][kz] = h2;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (PZ > 1) dft_small<PZ, true, false>(a[c]);
+#pragma unroll
+            for (int zz = 0; zz < PZ; ++zz)
+                if (zz < nz) S[(c * nz + zz) * g.rsy + ky] = a[c][zz];
+        }
+    }
+    __syncthreads();
+    fft_row<true, false, true>(myrow, Py, g.lpy, j, P.tw_py, 1, act);
+
+    for (int e = tid; e < nrow * ny; e += nth) {
+        const int r = e / ny, y = e - r * ny;
+        Wk[e] = S[r * g.rsy + y];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// block reduction of RED_NSLOT doubles (sum, except the max slot)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void block_reduce_store(double *v, double *scratch, double *out)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int s = 0; s < RED_NSLOT; ++s) {
+        double x = v[s];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double y = __shfl_down_sync(0xffffffffu, x, o);
+            x = (s == RED_T2MAX) ? fmax(x, y) : x + y;
+        }
+        if (lane == 0) scratch[warp * RED_NSLOT + s] = x;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int s = 0; s < RED_NSLOT; ++s) {
+            double x = lane < nw ? scratch[lane * RED_NSLOT + s] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double y = __shfl_down_sync(0xffffffffu, x, o);
+                x = (s == RED_T2MAX) ? fmax(x, y) : x + y;
+            }
+            if (lane == 0) out[s] = x;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_xinv
+// ---------------------------------------------------------------------------
+template <typename T, int MODE>
+__global__ void __launch_bounds__(768) k_xinv(Geom g, FieldPtrs<T> P, double hx0, double hx1, double hx2)
+{
+    typedef typename cvec<T>::type V;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *S = reinterpret_cast<V *>(smem_raw);
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int TY = g.TY, y0 = blockIdx.x * TY, z = blockIdx.y;
+    const int nx = g.nx, ny = g.ny, nz = g.nz, Hx = g.Hx;
+    const long N = g.N;
+
+    // complex-to-real preprocessing: Z[k] = (X[k] + X*[Hx-k]) + i conj(w^k) (X[k] - X*[Hx-k])
+    for (int e = tid; e < TY * 3 * Hx; e += nth) {
+        const int yl = e % TY, rest = e / TY, c = rest % 3, k = rest / 3;
+        const int y = y0 + yl;
+        V Z = czero<V>();
+        if (y < ny) {
+            const long base = ((long)c * nz + z) * ny + y;
+            const long strideK = (long)3 * nz * ny;
+            const V Xk = P.W[(long)k * strideK + base];
+            const V Xm = cconj(P.W[(long)(Hx - k) * strideK + base]);
+            const V sum = cadd(Xk, Xm), dif = csub(Xk, Xm);
+            const V t = cmulc(dif, P.tw_px[k]);  // conj(w^k) dif
+            Z.x = sum.x - t.y;
+            Z.y = sum.y + t.x;
+        }
+        S[(c * TY + yl) * g.rsx + k] = Z;
+    }
+    __syncthreads();
+    {
+        const int row = tid / g.Gx, j = tid - row * g.Gx;
+        const bool act = row < 3 * TY;
+        fft_row<true, false, true>(S + (act ? row : 0) * g.rsx, Hx, g.lhx, j, P.tw_px, 2, act);
+    }
+
+    // local terms
+    const MinState *st = P.st;
+    long k = 0;
+    int cur = 0;
+    const T *m;
+    if (MODE == MODE_MIN) {
+        k = st->k;
+        cur = st->base ^ (int)(k & 1);
+        m = P.mbuf[cur];
+        hx0 = st->Hext[0]; hx1 = st->Hext[1]; hx2 = st->Hext[2];
+    } else {
+        m = P.m_src;
+    }
+    const T he0 = (T)hx0, he1 = (T)hx1, he2 = (T)hx2;
+    const T cx = (T)g.cex_x, cy = (T)g.cex_y, cz = (T)g.cex_z, can = (T)g.can;
+    double red[RED_NSLOT];
+#pragma unroll
+    for (int s = 0; s < RED_NSLOT; ++s) red[s] = 0.0;
+
+    for (int e = tid; e < TY * nx; e += nth) {
+        const int yl = e / nx, x = e - yl * nx, y = y0 + yl;
+        if (y >= ny) continue;
+        const long n = ((long)z * ny + y) * nx + x;
+        const T d0 = reinterpret_cast<const T *>(S + (0 * TY + yl) * g.rsx)[x];
+        const T d1 = reinterpret_cast<const T *>(S + (1 * TY + yl) * g.rsx)[x];
+        const T d2 = reinterpret_cast<const T *>(S + (2 * TY + yl) * g.rsx)[x];
+        const T m0 = m[n], m1 = m[N + n], m2 = m[2 * N + n];
+        // exchange: sum over present neighbours of (m_j - m_i) / d^2 (free faces)
+        T e0 = 0, e1 = 0, e2 = 0;
+        if (x > 0)      { e0 += cx * (m[n - 1] - m0);  e1 += cx * (m[N + n - 1] - m1);  e2 += cx * (m[2 * N + n - 1] - m2); }
+        if (x < nx - 1) { e0 += cx * (m[n + 1] - m0);  e1 += cx * (m[N + n + 1] - m1);  e2 += cx * (m[2 * N + n + 1] - m2); }
+        if (y > 0)      { e0 += cy * (m[n - nx] - m0); e1 += cy * (m[N + n - nx] - m1); e2 += cy * (m[2 * N + n - nx] - m2); }
+        if (y < ny - 1) { e0 += cy * (m[n + nx] - m0); e1 += cy * (m[N + n + nx] - m1); e2 += cy * (m[2 * N + n + nx] - m2); }
+        const long sxy = (long)nx * ny;
+        if (z > 0)      { e0 += cz * (m[n - sxy] - m0); e1 += cz * (m[N + n - sxy] - m1); e2 += cz * (m[2 * N + n - sxy] - m2); }
+        if (z < nz - 1) { e0 += cz * (m[n + sxy] - m0); e1 += cz * (m[N + n + sxy] - m1); e2 += cz * (m[2 * N + n + sxy] - m2); }
+        // uniaxial anisotropy
+        const T Kv = P.Kc ? P.Kc[n] : (T)g.K;
+        T u0, u1, u2;
+        if (P.uc) { u0 = P.uc[n]; u1 = P.uc[N + n]; u2 = P.uc[2 * N + n]; }
+        else { u0 = (T)g.u[0]; u1 = (T)g.u[1]; u2 = (T)g.u[2]; }
+        const T mu = m0 * u0 + m1 * u1 + m2 * u2;
+        const T ka = can * Kv * mu;
+        const T H0 = d0 + e0 + ka * u0 + he0;
+        const T H1 = d1 + e1 + ka * u1 + he1;
+        const T H2 = d2 + e2 + ka * u2 + he2;
+        if (MODE == MODE_HEFF) {
+            P.H_out[n] = H0; P.H_out[N + n] = H1; P.H_out[2 * N + n] = H2;
+            continue;
+        }
+        red[RED_ED] += (double)(m0 * d0 + m1 * d1 + m2 * d2);
+        red[RED_EEX] += (double)(m0 * e0 + m1 * e1 + m2 * e2);
+        red[RED_EAN] += (double)(Kv * ((T)1 - mu * mu));
+        red[RED_EZ] += (double)(m0 * he0 + m1 * he1 + m2 * he2);
+        red[RED_MX] += (double)m0; red[RED_MY] += (double)m1; red[RED_MZ] += (double)m2;
+        if (MODE == MODE_MIN) {
+            // a = m x H, g = m x a = m x (m x H)
+            const T a0 = m1 * H2 - m2 * H1, a1 = m2 * H0 - m0 * H2, a2 = m0 * H1 - m1 * H0;
+            const T g0 = m1 * a2 - m2 * a1, g1 = m2 * a0 - m0 * a2, g2 = m0 * a1 - m1 * a0;
+            red[RED_T2MAX] = fmax(red[RED_T2MAX], (double)(a0 * a0 + a1 * a1 + a2 * a2));
+            T *gout = P.gbuf[(int)(k & 1)];
+            if (k > 0) {
+                const T *mp = P.mbuf[cur ^ 1];
+                const T *gq = P.gbuf[(int)((k - 1) & 1)];  // g_{k-1}
+                const T s0 = m0 - mp[n], s1 = m1 - mp[N + n], s2 = m2 - mp[2 * N + n];
+                const T y0v = g0 - gq[n], y1v = g1 - gq[N + n], y2v = g2 - gq[2 * N + n];
+                red[RED_SS] += (double)(s0 * s0 + s1 * s1 + s2 * s2);
+                red[RED_SY] += (double)(s0 * y0v + s1 * y1v + s2 * y2v);
+                red[RED_YY] += (double)(y0v * y0v + y1v * y1v + y2v * y2v);
+            }
+            gout[n] = g0; gout[N + n] = g1; gout[2 * N + n] = g2;
+        }
+    }
+    if (MODE == MODE_HEFF) return;
+    __syncthreads();  // the FFT rows are no longer needed: reuse shared memory as scratch
+    double *scratch = reinterpret_cast<double *>(smem_raw);
+    block_reduce_store(red, scratch, P.partials + (long)(blockIdx.y * gridDim.x + blockIdx.x) * RED_NSLOT);
+}
+
+// ---------------------------------------------------------------------------
+// k_reduce: one CTA
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_reduce(const double *partials, int nblk, MinState *st, Geom g,
+                                                cudaGraphConditionalHandle h, int use_cond, int body_kernels)
+{
+    __shared__ double scratch[8 * RED_NSLOT];
+    __shared__ double tot[RED_NSLOT];
+    double v[RED_NSLOT];
+#pragma unroll
+    for (int s = 0; s < RED_NSLOT; ++s) v[s] = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+#pragma unroll
+        for (int s = 0; s < RED_NSLOT; ++s) {
+            const double x = partials[(long)b * RED_NSLOT + s];
+            v[s] = (s == RED_T2MAX) ? fmax(v[s], x) : v[s] + x;
+        }
+    }
+    block_reduce_store(v, scratch, tot);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+
+    const double V = g.dx * g.dy * g.dz, Ms = g.Ms;
+    const double Ed = -0.5 * MM_MU0 * Ms * V * tot[RED_ED];
+    const double Eex = -0.5 * MM_MU0 * Ms * V * tot[RED_EEX];
+    const double Ean = V * tot[RED_EAN];
+    const double Ez = -MM_MU0 * Ms * V * tot[RED_EZ];
+    st->energy[0] = Ed; st->energy[1] = Eex; st->energy[2] = Ean; st->energy[3] = Ez;
+    st->energy[4] = Ed + Eex + Ean + Ez;
+    st->mavg[0] = tot[RED_MX] / (double)g.N;
+    st->mavg[1] = tot[RED_MY] / (double)g.N;
+    st->mavg[2] = tot[RED_MZ] / (double)g.N;
+    if (MODE != MODE_MIN) return;
+
+    const long k = st->k;
+    const double tmax = sqrt(tot[RED_T2MAX]);
+    st->max_torque = tmax / Ms;
+    st->evals = k + 1;
+    st->launches += body_kernels;
+    if (k == 0) st->t_start_ns = globaltimer_ns();
+    int stop = 1;
+    const bool finite = isfinite(tmax) && isfinite(st->energy[4]) &&
+                        (k == 0 || (isfinite(tot[RED_SS]) && isfinite(tot[RED_SY]) && isfinite(tot[RED_YY])));
+    if (!finite) {
+        st->status = MMS_NONFINITE;
+    } else if (tmax < st->tol_abs) {
+        st->status = MMS_CONVERGED;
+    } else if (k >= st->max_iter) {
+        st->status = MMS_MAXITER;
+    } else if (st->timeout_ns && globaltimer_ns() - st->t_start_ns > st->timeout_ns) {
+        st->status = MMS_TIMEOUT;
+    } else {
+        double tau;
+        if (k == 0) {
+            tau = st->tau0;
+        } else {
+            const double ss = tot[RED_SS], sy = tot[RED_SY], yy = tot[RED_YY];
+            tau = (k & 1) ? ss / sy : sy / yy;
+            if (!(isfinite(tau) && tau > 0.0)) tau = sqrt(ss / yy);
+            if (!(isfinite(tau) && tau > 0.0)) tau = st->tau0;
+        }
+        st->tau = tau;
+        st->k = k + 1;
+        stop = 0;
+    }
+    if (use_cond) cudaGraphSetConditional(h, stop ? 0u : 1u);
+}
+
+__global__ void k_init_state(MinState *st, double tau0, double tol_abs, double h0, double h1, double h2,
+                             long max_iter, int step_kind, unsigned long long timeout_ns, int reset_base)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (reset_base) st->base = 0;
+    else st->base = st->base ^ (int)(st->k & 1);   // continue from the previous result
+    st->tau0 = tau0; st->tol_abs = tol_abs;
+    st->Hext[0] = h0; st->Hext[1] = h1; st->Hext[2] = h2;
+    st->max_iter = max_iter; st->step_kind = step_kind;
+    st->timeout_ns = timeout_ns; st->t_start_ns = 0;
+    st->k = 0; st->tau = tau0; st->status = MMS_RUNNING; st->evals = 0; st->launches = 1;
+    st->max_torque = 0;
+}
+
+__global__ void k_record(const MinState *st, StepRecord *rec, int step)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    StepRecord r;
+    r.mavg[0] = st->mavg[0]; r.mavg[1] = st->mavg[1]; r.mavg[2] = st->mavg[2];
+    r.max_torque = st->max_torque; r.energy = st->energy[4];
+    r.iters = st->k; r.evals = st->evals; r.launches = st->launches + 1; r.status = st->status;
+    rec[step] = r;
+}
+
+template <typename T>
+__global__ void k_copy_result(const MinState *st, const T *b0, const T *b1, T *dst, long n3)
+{
+    const T *src = (st->base ^ (int)(st->k & 1)) ? b1 : b0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n3; i += (long)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+template <typename T>
+__global__ void k_twiddle(typename cvec<T>::type *tw, int L)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L) return;
+    double s, c;
+    sincospi(2.0 * (double)t / (double)L, &s, &c);
+    typename cvec<T>::type w;
+    w.x = (T)c; w.y = (T)(-s);
+    tw[t] = w;
+}
+
+template <typename T>
+__global__ void k_convert(T *dst, const double *src, long n)
+{
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        dst[i] = (T)src[i];
+}
+
+// ---------------------------------------------------------------------------
+// host-side launch helpers
+// ---------------------------------------------------------------------------
+template <typename T> FieldPtrs<T> make_ptrs(mm_problem *p)
+{
+    typedef typename cvec<T>::type V;
+    FieldPtrs<T> P;
+    P.m_src = nullptr; P.H_out = nullptr;
+    P.mbuf[0] = (T *)p->mbuf[0]; P.mbuf[1] = (T *)p->mbuf[1];
+    P.gbuf[0] = (T *)p->gbuf[0]; P.gbuf[1] = (T *)p->gbuf[1];
+    P.W = (V *)p->W; P.Nhat = (const T *)p->Nhat;
+    P.tw_px = (const V *)p->tw_px; P.tw_py = (const V *)p->tw_py; P.tw_pz = (const V *)p->tw_pz;
+    P.Kc = (const T *)p->Kc; P.uc = (const T *)p->uc;
+    P.partials = p->partials; P.st = p->st; P.Hext = nullptr;
+    return P;
+}
+
+template <typename T> size_t smem_x_t(const Geom &g)
+{
+    size_t b = (size_t)3 * g.TY * g.rsx * sizeof(typename cvec<T>::type);
+    size_t r = (size_t)32 * RED_NSLOT * sizeof(double);
+    return b > r ? b : r;
+}
+template <typename T> size_t smem_yz_t(const Geom &g)
+{
+    return (size_t)3 * g.nz * g.rsy * sizeof(typename cvec<T>::type);
+}
+
+static inline int round32(int n) { return (n + 31) & ~31; }
+template <typename T> int threads_x(const Geom &g) { return round32(3 * g.TY * g.Gx); }
+template <typename T> int threads_yz(const Geom &g) { return round32(3 * g.nz * g.Gy); }
+
+template <typename T, int PZ>
+cudaError_t launch_yz(const Geom &g, const FieldPtrs<T> &P, cudaStream_t s)
+{
+    k_yz<T, PZ><<<g.C, threads_yz<T>(g), smem_yz_t<T>(g), s>>>(g, P);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_yz_any(const Geom &g, const FieldPtrs<T> &P, cudaStream_t s)
+{
+    switch (g.Pz) {
+    case 1: return launch_yz<T, 1>(g, P, s);
+    case 2: return launch_yz<T, 2>(g, P, s);
+    case 4: return launch_yz<T, 4>(g, P, s);
+    case 8: return launch_yz<T, 8>(g, P, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T, int PZ> cudaError_t set_yz_attr(size_t smem)
+{
+    return cudaFuncSetAttribute(k_yz<T, PZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <typename T> cudaError_t configure_t(mm_problem *p)
+{
+    const size_t sx = smem_x_t<T>(p->g), syz = smem_yz_t<T>(p->g);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_xfwd<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx))) return e;
+    if ((e = cudaFuncSetAttribute(k_xfwd<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx))) return e;
+    if ((e = cudaFuncSetAttribute(k_xinv<T, MODE_HEFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx))) return e;
+    if ((e = cudaFuncSetAttribute(k_xinv<T, MODE_ENERGY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx))) return e;
+    if ((e = cudaFuncSetAttribute(k_xinv<T, MODE_MIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx))) return e;
+    switch (p->g.Pz) {
+    case 1: return set_yz_attr<T, 1>(syz);
+    case 2: return set_yz_attr<T, 2>(syz);
+    case 4: return set_yz_attr<T, 4>(syz);
+    case 8: return set_yz_attr<T, 8>(syz);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Field chain for MODE_HEFF / MODE_ENERGY on caller-provided m (and H).
+template <typename T>
+cudaError_t heff_chain_t(mm_problem *p, const void *m, void *H, const double *hext, int mode, cudaStream_t s)
+{
+    const Geom &g = p->g;
+    FieldPtrs<T> P = make_ptrs<T>(p);
+    P.m_src = (const T *)m;
+    P.H_out = (T *)H;
+    const dim3 gx((g.ny + g.TY - 1) / g.TY, g.nz);
+    const size_t sx = smem_x_t<T>(g);
+    k_xfwd<T, false><<<gx, threads_x<T>(g), sx, s>>>(g, P);
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    if ((e = launch_yz_any<T>(g, P, s))) return e;
+    if (mode == MODE_HEFF)
+        k_xinv<T, MODE_HEFF><<<gx, threads_x<T>(g), sx, s>>>(g, P, hext[0], hext[1], hext[2]);
+    else
+        k_xinv<T, MODE_ENERGY><<<gx, threads_x<T>(g), sx, s>>>(g, P, hext[0], hext[1], hext[2]);
+    if ((e = cudaGetLastError())) return e;
+    if (mode == MODE_ENERGY) {
+        k_reduce<MODE_ENERGY><<<1, 256, 0, s>>>(p->partials, p->nblk_x, p->st, g, 0, 0, 0);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+template <typename T>
+cudaError_t min_body_t(mm_problem *p, cudaGraphConditionalHandle h, cudaStream_t s, int use_cond)
+{
+    const Geom &g = p->g;
+    FieldPtrs<T> P = make_ptrs<T>(p);
+    const dim3 gx((g.ny + g.TY - 1) / g.TY, g.nz);
+    const size_t sx = smem_x_t<T>(g);
+    k_xfwd<T, true><<<gx, threads_x<T>(g), sx, s>>>(g, P);
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    if ((e = launch_yz_any<T>(g, P, s))) return e;
+    k_xinv<T, MODE_MIN><<<gx, threads_x<T>(g), sx, s>>>(g, P, 0.0, 0.0, 0.0);
+    if ((e = cudaGetLastError())) return e;
+    k_reduce<MODE_MIN><<<1, 256, 0, s>>>(p->partials, p->nblk_x, p->st, g, h, use_cond, 4);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t stage_times_t(mm_problem *p, int reps, double *ms, cudaStream_t s)
+{
+    const Geom &g = p->g;
+    FieldPtrs<T> P = make_ptrs<T>(p);
+    const dim3 gx((g.ny + g.TY - 1) / g.TY, g.nz);
+    const size_t sx = smem_x_t<T>(g);
+    cudaEvent_t ev[5];
+    for (int i = 0; i < 5; ++i)
+        if (cudaEventCreate(&ev[i])) return cudaGetLastError();
+    double acc[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < reps && !e; ++r) {
+        cudaEventRecord(ev[0], s);
+        k_xfwd<T, true><<<gx, threads_x<T>(g), sx, s>>>(g, P);
+        cudaEventRecord(ev[1], s);
+        launch_yz_any<T>(g, P, s);
+        cudaEventRecord(ev[2], s);
+        k_xinv<T, MODE_MIN><<<gx, threads_x<T>(g), sx, s>>>(g, P, 0.0, 0.0, 0.0);
+        cudaEventRecord(ev[3], s);
+        k_reduce<MODE_MIN><<<1, 256, 0, s>>>(p->partials, p->nblk_x, p->st, g, 0, 0, 4);
+        cudaEventRecord(ev[4], s);
+        if ((e = cudaGetLastError())) break;
+        if ((e = cudaEventSynchronize(ev[4]))) break;
+        for (int i = 0; i < 4; ++i) {
+            float t = 0;
+            cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+            acc[i] += t;
+        }
+    }
+    for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+    for (int i = 0; i < 4; ++i) ms[i] = acc[i] / (reps > 0 ? reps : 1);
+    return e;
+}
+
+} // namespace
+
+// ---------------------------------------------------------------------------
+// exported to api.cu
+// ---------------------------------------------------------------------------
+#define DISPATCH(p, expr_d, expr_f) ((p)->precision == MM_FP64 ? (expr_d) : (expr_f))
+
+size_t mm_smem_x(const mm_problem *p) { return DISPATCH(p, smem_x_t<double>(p->g), smem_x_t<float>(p->g)); }
+size_t mm_smem_yz(const mm_problem *p) { return DISPATCH(p, smem_yz_t<double>(p->g), smem_yz_t<float>(p->g)); }
+
+int mm_heff_configure(mm_problem *p)
+{
+    cudaError_t e = DISPATCH(p, configure_t<double>(p), configure_t<float>(p));
+    if (e) { mm_set_cuda_error(e, "cudaFuncSetAttribute"); return MM_ERR_CUDA; }
+    return MM_OK;
+}
+
+int mm_launch_field(mm_problem *p, const void *m, void *H, const double *hext, int mode, cudaStream_t s)
+{
+    cudaError_t e = DISPATCH(p, heff_chain_t<double>(p, m, H, hext, mode, s),
+                             heff_chain_t<float>(p, m, H, hext, mode, s));
+    if (e) { mm_set_cuda_error(e, "field kernels"); return MM_ERR_CUDA; }
+    return MM_OK;
+}
+
+int mm_launch_min_body(mm_problem *p, cudaGraphConditionalHandle h, cudaStream_t s, int use_cond)
+{
+    cudaError_t e = DISPATCH(p, min_body_t<double>(p, h, s, use_cond), min_body_t<float>(p, h, s, use_cond));
+    if (e) { mm_set_cuda_error(e, "minimiser body"); return MM_ERR_CUDA; }
+    return MM_OK;
+}
+
+int mm_kernel_stage_times(mm_problem *p, int reps, double *ms, const char **names, int *count, cudaStream_t s)
+{
+    static const char *nm[4] = {"xfwd_step", "yz_conv", "xinv_local", "reduce_bb"};
+    if (*count < 4) return MM_ERR_ARG;
+    cudaError_t e = DISPATCH(p, stage_times_t<double>(p, reps, ms, s), stage_times_t<float>(p, reps, ms, s));
+    if (e) { mm_set_cuda_error(e, "stage timing"); return MM_ERR_CUDA; }
+    for (int i = 0; i < 4; ++i) names[i] = nm[i];
+    *count = 4;
+    return MM_OK;
+}
+
+int mm_launch_init_state(mm_problem *p, const double Hext[3], const mm_min_opts *o, int reset_base, cudaStream_t s)
+{
+    double tau0 = o->tau0 > 0 ? o->tau0 : 1e-2 / p->g.Ms;
+    unsigned long long to = o->timeout_s > 0 ? (unsigned long long)(o->timeout_s * 1e9) : 0ull;
+    k_init_state<<<1, 32, 0, s>>>(p->st, tau0, o->tol * p->g.Ms, Hext[0], Hext[1], Hext[2], o->max_iter,
+                                  o->step_kind, to, reset_base);
+    cudaError_t e = cudaGetLastError();
+    if (e) { mm_set_cuda_error(e, "k_init_state"); return MM_ERR_CUDA; }
+    return MM_OK;
+}
+
+int mm_launch_record(mm_problem *p, int step, cudaStream_t s)
+{
+    k_record<<<1, 32, 0, s>>>(p->st, p->rec_dev, step);
+    cudaError_t e = cudaGetLastError();
+    if (e) { mm_set_cuda_error(e, "k_record"); return MM_ERR_CUDA; }
+    return MM_OK;
+}
+
+int mm_launch_copy_result(mm_problem *p, void *dst, cudaStream_t s)
+{
+    const long n3 = 3 * p->g.N;
+    const int blocks = (int)((n3 + 255) / 256 < 152 * 8 ? (n3 + 255) / 256 : 152 * 8);
+    if (p->precision == MM_FP64)
+        k_copy_result<double><<<blocks, 256, 0, s>>>(p->st, (const double *)p->mbuf[0],
+                                                    (const double *)p->mbuf[1], (double *)dst, n3);
+    else
+        k_copy_result<float><<<blocks, 256, 0, s>>>(p->st, (const float *)p->mbuf[0],
+                                                   (const float *)p->mbuf[1], (float *)dst, n3);
+    cudaError_t e = cudaGetLastError();
+    if (e) { mm_set_cuda_error(e, "k_copy_result"); return MM_ERR_CUDA; }
+    return MM_OK;
+}
+
+int mm_launch_twiddles(mm_problem *p, cudaStream_t s)
+{
+    const Geom &g = p->g;
+    const int L[3] = {g.Px, g.Py, g.Pz};
+    void *dst[3] = {p->tw_px, p->tw_py, p->tw_pz};
+    for (int i = 0; i < 3; ++i) {
+        const int blocks = (L[i] + 255) / 256;
+        if (p->precision == MM_FP64) k_twiddle<double><<<blocks, 256, 0, s>>>((double2 *)dst[i], L[i]);
+        else k_twiddle<float><<<blocks, 256, 0, s>>>((float2 *)dst[i], L[i]);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e) { mm_set_cuda_error(e, "k_twiddle"); return MM_ERR_CUDA; }
+    return MM_OK;
+}
+
+int mm_launch_convert(mm_problem *p, void *dst, const double *src, long n, cudaStream_t s)
+{
+    const int blocks = (int)((n + 255) / 256 < 1216 ? (n + 255) / 256 : 1216);
+    if (p->precision == MM_FP64) k_convert<double><<<blocks, 256, 0, s>>>((double *)dst, src, n);
+    else k_convert<float><<<blocks, 256, 0, s>>>((float *)dst, src, n);
+    cudaError_t e = cudaGetLastError();
+    if (e) { mm_set_cuda_error(e, "k_convert"); return MM_ERR_CUDA; }
+    return MM_OK;
+}

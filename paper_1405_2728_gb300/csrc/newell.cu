@@ -1,0 +1,225 @@
+// Demagnetisation tensor setup (once per geometry).
+//
+// The demagnetisation field of Section 3 is a discrete convolution with the
+// cell-averaged tensor of Newell, Williams and Dunlop (J. Geophys. Res. 98
+// (1993) 9551):
+//   N_xx(X,Y,Z) = 1/(4 pi dx dy dz) sum_{e in {-1,0,1}^3} c(e) f(X+e1 dx, Y+e2 dy, Z+e3 dz),
+//   c(e) = 8, -4, 2, -1 for 0, 1, 2, 3 non-zero entries of e,
+// N_yy, N_zz by permuting coordinates, N_xy, N_xz, N_yz likewise from g.
+//
+//  k_newell_table    f and g (six permutations) on the (nx+1)(ny+1)(nz+1)
+//                    non-negative lattice, in double-double (dd.cuh): the
+//                    second difference cancels ~R^6 of their magnitude.
+//  k_newell_stencil  the 27-point sums in double-double, rounded to double:
+//                    the first octant of offsets, [6][nz][ny][nx].
+//  k_place / k_fft_strided / k_extract
+//                    the tensor placed circularly on the zero-padded grid
+//                    (offsets -(n-1)..(n-1), unused entries 0), its 3-D FFT in
+//                    double, and the real parts (all six spectra are real by
+//                    the even/odd symmetry) of the octant kx <= Px/2,
+//                    ky <= Py/2, kz <= Pz/2, scaled by -Ms/(Px Py Pz) so that
+//                    the convolution kernels need no other normalisation.
+#include "common.cuh"
+#include "dd.cuh"
+#include "fft.cuh"
+
+namespace {
+
+__global__ void k_newell_table(int nx, int ny, int nz, double hx, double hy, double hz, dd_t *T)
+{
+    const long ax = nx + 1, ay = ny + 1, az = nz + 1, na = ax * ay * az;
+    for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < na; p += (long)gridDim.x * blockDim.x) {
+        const long a = p % ax, b = (p / ax) % ay, c = p / (ax * ay);
+        // lattice coordinates are exact in dd: integer times a double
+        const dd_t X = dd_two_prod((double)a, hx), Y = dd_two_prod((double)b, hy), Z = dd_two_prod((double)c, hz);
+        T[0 * na + p] = dd_newell_f(X, Y, Z);
+        T[1 * na + p] = dd_newell_f(Y, X, Z);
+        T[2 * na + p] = dd_newell_f(Z, Y, X);
+        T[3 * na + p] = dd_newell_g(X, Y, Z);
+        T[4 * na + p] = dd_newell_g(X, Z, Y);
+        T[5 * na + p] = dd_newell_g(Y, Z, X);
+    }
+}
+
+__global__ void k_newell_stencil(int nx, int ny, int nz, double hx, double hy, double hz, const dd_t *T,
+                                 double *out)
+{
+    const long ax = nx + 1, ay = ny + 1, az = nz + 1, na = ax * ay * az;
+    const long nn = (long)nx * ny * nz;
+    // 1 / (4 pi hx hy hz) in dd
+    const dd_t pi = dd_make(DD_PI_HI, DD_PI_LO);
+    const dd_t vol = dd_mul(dd_mul(dd_from(hx), dd_from(hy)), dd_from(hz));
+    const dd_t norm = dd_div(dd_from(1.0), dd_mul(dd_ldexp(pi, 2), vol));
+    const int W[4] = {8, -4, 2, -1};
+    for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < nn; p += (long)gridDim.x * blockDim.x) {
+        const long i = p % nx, j = (p / nx) % ny, k = p / ((long)nx * ny);
+        dd_t s[6];
+        for (int c = 0; c < 6; ++c) s[c] = dd_from(0.0);
+        for (int e1 = -1; e1 <= 1; ++e1)
+            for (int e2 = -1; e2 <= 1; ++e2)
+                for (int e3 = -1; e3 <= 1; ++e3) {
+                    const double w = (double)W[(e1 != 0) + (e2 != 0) + (e3 != 0)];
+                    const long a = i + e1, b = j + e2, c3 = k + e3;
+                    const long q = ((c3 < 0 ? -c3 : c3) * ay + (b < 0 ? -b : b)) * ax + (a < 0 ? -a : a);
+                    const double sa = a < 0 ? -1.0 : 1.0, sb = b < 0 ? -1.0 : 1.0, sc = c3 < 0 ? -1.0 : 1.0;
+                    s[0] = dd_add(s[0], dd_mul_d(T[0 * na + q], w));
+                    s[1] = dd_add(s[1], dd_mul_d(T[1 * na + q], w));
+                    s[2] = dd_add(s[2], dd_mul_d(T[2 * na + q], w));
+                    s[3] = dd_add(s[3], dd_mul_d(T[3 * na + q], w * sa * sb));  // g(x,y,z): odd in x, y
+                    s[4] = dd_add(s[4], dd_mul_d(T[4 * na + q], w * sa * sc));  // g(x,z,y): odd in x, z
+                    s[5] = dd_add(s[5], dd_mul_d(T[5 * na + q], w * sb * sc));  // g(y,z,x): odd in y, z
+                }
+        for (int c = 0; c < 6; ++c) {
+            const dd_t v = dd_mul(s[c], norm);
+            out[c * nn + p] = v.hi + v.lo;
+        }
+    }
+}
+
+// parity of component c under sign flips of the x, y, z offsets
+__device__ __forceinline__ double comp_sign(int c, long i, long j, long k)
+{
+    const bool nx_ = i < 0, ny_ = j < 0, nz_ = k < 0;
+    bool flip = false;
+    if (c == 3) flip = nx_ ^ ny_;
+    else if (c == 4) flip = nx_ ^ nz_;
+    else if (c == 5) flip = ny_ ^ nz_;
+    return flip ? -1.0 : 1.0;
+}
+
+__global__ void k_place(int c, int nx, int ny, int nz, int Px, int Py, int Pz, const double *Noct, double2 *F)
+{
+    const long tot = (long)Px * Py * Pz;
+    const long nn = (long)nx * ny * nz;
+    for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < tot; p += (long)gridDim.x * blockDim.x) {
+        const long ii = p % Px, jj = (p / Px) % Py, kk = p / ((long)Px * Py);
+        const long i = ii < nx ? ii : (ii > Px - nx ? ii - Px : Px);
+        const long j = jj < ny ? jj : (jj > Py - ny ? jj - Py : Py);
+        const long k = kk < nz ? kk : (kk > Pz - nz ? kk - Pz : Pz);
+        double v = 0.0;
+        if (i != Px && j != Py && k != Pz) {
+            const long ai = i < 0 ? -i : i, aj = j < 0 ? -j : j, ak = k < 0 ? -k : k;
+            v = comp_sign(c, i, j, k) * Noct[c * nn + (ak * ny + aj) * nx + ai];
+        }
+        F[p] = make_double2(v, 0.0);
+    }
+}
+
+__global__ void k_twiddle_d(double2 *tw, int L)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L) return;
+    double s, c;
+    sincospi(2.0 * (double)t / (double)L, &s, &c);
+    tw[t] = make_double2(c, -s);
+}
+
+// Forward FFT of rows of length L along a strided axis: row r starts at
+// base(r) = (r % inner) + (r / inner) * outer_stride and its elements are
+// `stride` apart.  One CTA per row.
+__global__ void k_fft_strided(double2 *F, int L, int logL, long stride, long inner, long outer_stride,
+                              const double2 *tw)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2 *S = reinterpret_cast<double2 *>(smem_raw);
+    const long r = blockIdx.x;
+    const long base = (r % inner) + (r / inner) * outer_stride;
+    for (int t = threadIdx.x; t < L; t += blockDim.x) S[t] = F[base + t * stride];
+    __syncthreads();
+    const int G = L >= 8 ? L / 8 : 1;
+    const bool act = threadIdx.x < G;
+    fft_row<false, false, false>(S, L, logL, act ? (int)threadIdx.x : 0, tw, 1, act);
+    __syncthreads();
+    for (int t = threadIdx.x; t < L; t += blockDim.x) F[base + t * stride] = S[t];
+}
+
+template <typename T>
+__global__ void k_extract(int c, int Px, int Py, int Pz, const double2 *F, double scale, T *Nhat)
+{
+    const int hx = Px / 2, hy = Py / 2, hz = Pz / 2;
+    const long tot = (long)(hx + 1) * (hy + 1) * (hz + 1);
+    for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < tot; p += (long)gridDim.x * blockDim.x) {
+        const long ky = p % (hy + 1), kz = (p / (hy + 1)) % (hz + 1), kx = p / ((long)(hy + 1) * (hz + 1));
+        const double v = F[(kz * Py + ky) * Px + kx].x;
+        Nhat[p * 6 + c] = (T)(scale * v);
+    }
+}
+
+int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
+
+} // namespace
+
+// Newell octant on the device: N_dev [6][nz][ny][nx] doubles.
+int mm_newell_device(const mm_grid *gr, double *N_dev, cudaStream_t s)
+{
+    double h = gr->dx;
+    if (gr->dy > h) h = gr->dy;
+    if (gr->dz > h) h = gr->dz;
+    const double hx = gr->dx / h, hy = gr->dy / h, hz = gr->dz / h;
+    const long na = (long)(gr->nx + 1) * (gr->ny + 1) * (gr->nz + 1);
+    const long nn = (long)gr->nx * gr->ny * gr->nz;
+    dd_t *T = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&T, sizeof(dd_t) * 6 * (size_t)na, s);
+    if (e) { mm_set_cuda_error(e, "cudaMallocAsync(newell table)"); return MM_ERR_OOM; }
+    const int bt = 128;
+    long blocks = (na + bt - 1) / bt;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    k_newell_table<<<(int)blocks, bt, 0, s>>>(gr->nx, gr->ny, gr->nz, hx, hy, hz, T);
+    blocks = (nn + bt - 1) / bt;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    k_newell_stencil<<<(int)blocks, bt, 0, s>>>(gr->nx, gr->ny, gr->nz, hx, hy, hz, T, N_dev);
+    e = cudaGetLastError();
+    cudaFreeAsync(T, s);
+    if (e) { mm_set_cuda_error(e, "newell kernels"); return MM_ERR_CUDA; }
+    return MM_OK;
+}
+
+// Tensor spectra into p->Nhat ([Px/2+1][Pz/2+1][Py/2+1][6], precision of p).
+int mm_tensor_spectrum(mm_problem *p, const double *N_dev, cudaStream_t s)
+{
+    const Geom &g = p->g;
+    const long tot = (long)g.Px * g.Py * g.Pz;
+    double2 *F = nullptr, *tw = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&F, sizeof(double2) * tot, s);
+    if (e) { mm_set_cuda_error(e, "cudaMallocAsync(tensor fft)"); return MM_ERR_OOM; }
+    e = cudaMallocAsync((void **)&tw, sizeof(double2) * (g.Px + g.Py + g.Pz), s);
+    if (e) { cudaFreeAsync(F, s); mm_set_cuda_error(e, "cudaMallocAsync(twiddles)"); return MM_ERR_OOM; }
+    double2 *twx = tw, *twy = tw + g.Px, *twz = tw + g.Px + g.Py;
+    k_twiddle_d<<<(g.Px + 255) / 256, 256, 0, s>>>(twx, g.Px);
+    k_twiddle_d<<<(g.Py + 255) / 256, 256, 0, s>>>(twy, g.Py);
+    k_twiddle_d<<<(g.Pz + 255) / 256, 256, 0, s>>>(twz, g.Pz);
+    const double scale = -g.Ms / ((double)g.Px * g.Py * g.Pz);
+    const int L[3] = {g.Px, g.Py, g.Pz};
+    const long stride[3] = {1, g.Px, (long)g.Px * g.Py};
+    const long rows[3] = {(long)g.Py * g.Pz, (long)g.Px * g.Pz, (long)g.Px * g.Py};
+    // row r -> base: x: r*Px; y: (r % Px) + (r / Px) * Px*Py; z: r
+    const long inner[3] = {1, g.Px, (long)g.Px * g.Py};
+    const long outer[3] = {g.Px, (long)g.Px * g.Py, 0};
+    const double2 *tws[3] = {twx, twy, twz};
+    long blocks = (tot + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    const long ext = (long)(g.Px / 2 + 1) * (g.Py / 2 + 1) * (g.Pz / 2 + 1);
+    long eblocks = (ext + 255) / 256;
+    if (eblocks > 152 * 32) eblocks = 152 * 32;
+    for (int c = 0; c < 6 && !e; ++c) {
+        k_place<<<(int)blocks, 256, 0, s>>>(c, g.nx, g.ny, g.nz, g.Px, g.Py, g.Pz, N_dev, F);
+        for (int a = 0; a < 3; ++a) {
+            if (L[a] == 1) continue;
+            const int thr = ((L[a] >= 8 ? L[a] / 8 : 1) + 31) & ~31;
+            const size_t sm = sizeof(double2) * L[a];
+            if (sm > 48 * 1024)
+                cudaFuncSetAttribute(k_fft_strided, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            k_fft_strided<<<(unsigned)rows[a], thr, sm, s>>>(F, L[a], ilog2(L[a]), stride[a], inner[a],
+                                                             outer[a] ? outer[a] : 1, tws[a]);
+        }
+        if (p->precision == MM_FP64)
+            k_extract<double><<<(int)eblocks, 256, 0, s>>>(c, g.Px, g.Py, g.Pz, F, scale, (double *)p->Nhat);
+        else
+            k_extract<float><<<(int)eblocks, 256, 0, s>>>(c, g.Px, g.Py, g.Pz, F, scale, (float *)p->Nhat);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(F, s);
+    cudaFreeAsync(tw, s);
+    if (e) { mm_set_cuda_error(e, "tensor spectrum"); return MM_ERR_CUDA; }
+    return MM_OK;
+}

@@ -1,0 +1,113 @@
+"""GPU parity of the minimiser (Section 2) and the hysteresis driver
+(Section 4) through the C ABI against the CPU oracle.
+
+Iterations: identical up to rounding for a fixed number of steps (sums are
+taken in a different order on the two sides, so trajectories agree to ~1e-9,
+not bit for bit).  Converged results: same stop rule; switching field within
+one field step and remanence within 1e-3 over a full loop."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import micromag as om
+from paper_1405_2728_gb300 import inputs
+from gpu_cases import dev, make_pair, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def small_film(mm, **kw):
+    w = inputs.film_32x16x1()
+    prob, oprob = make_pair(mm, w.nx, w.ny, w.nz, (w.dx, w.dy, w.dz), Ms=w.Ms, A=w.A, K=w.K, **kw)
+    return w, prob, oprob
+
+
+@pytest.mark.parametrize("step", [0, 1])
+def test_fixed_steps_follow_the_oracle(mmlib, step):
+    w, prob, oprob = small_film(mmlib)
+    m0 = inputs.random_unit_m(oprob.shape, 21)
+    H = w.fields()[40]
+    m = dev(m0)
+    opts = mmlib.make_opts(tol=0.0, max_iter=25, step_kind=step)
+    st, r = mmlib.mm_minimize(prob, m, H, opts)
+    assert st == mmlib.MM_ERR_NOT_CONVERGED and r.iters == 25 and r.heff_evals == 26
+    ref = om.minimize(oprob, m0, H, om.Demag(oprob), tol=0.0, max_iter=25,
+                      step="cayley" if step == 0 else "normalize")
+    assert rel_l2(m.cpu().numpy(), ref.m) <= 1e-8
+    assert abs(r.max_torque - ref.max_torque) <= 1e-7 * ref.max_torque
+    assert np.max(np.abs(np.linalg.norm(m.cpu().numpy(), axis=0) - 1)) < 1e-14
+
+
+def test_converged_minimum_matches_oracle(mmlib):
+    w, prob, oprob = small_film(mmlib)
+    m0 = w.initial_m()
+    H = w.fields()[30]   # +20 mT: far from switching, so the minimum is unique from this start
+    d = om.Demag(oprob)
+    ref = om.minimize(oprob, m0, H, d, tol=w.tol)
+    m = dev(m0)
+    st, r = mmlib.mm_minimize(prob, m, H, mmlib.make_opts(tol=w.tol))
+    assert st == mmlib.MM_OK and r.converged and r.max_torque < w.tol
+    assert abs(r.iters - ref.iters) <= max(3, ref.iters // 10)
+    got = m.cpu().numpy()
+    assert np.max(np.abs(got - ref.m)) < 1e-4
+    E = om.energy(oprob, got, H, d)["total"]
+    assert abs(r.energy - E) <= 1e-10 * abs(E)
+    assert abs(E - om.energy(oprob, ref.m, H, d)["total"]) <= 1e-8 * abs(E)
+    assert np.max(np.abs(np.linalg.norm(got, axis=0) - 1)) < 1e-13
+
+
+def test_status_codes_from_the_device_loop(mmlib):
+    w, prob, oprob = small_film(mmlib)
+    m = dev(inputs.random_unit_m(oprob.shape, 2))
+    # wall-clock limit: the device loop stops and reports it (no waiting on the host)
+    st, r = mmlib.mm_minimize(prob, m, (0, 0, 0), mmlib.make_opts(tol=0.0, max_iter=10**6, timeout_s=1e-9))
+    assert st == mmlib.MM_ERR_TIMEOUT and 0 <= r.iters < 10 and r.heff_evals == r.iters + 1
+    # a non-finite input is reported, not propagated silently
+    bad = inputs.random_unit_m(oprob.shape, 3)
+    bad[0, 0, 3, 5] = np.nan
+    st, r = mmlib.mm_minimize(prob, dev(bad), (0, 0, 0), mmlib.make_opts())
+    assert st == mmlib.MM_ERR_NONFINITE
+    # the problem is still usable afterwards
+    st, r = mmlib.mm_minimize(prob, m, w.fields()[0], mmlib.make_opts(tol=w.tol))
+    assert st == mmlib.MM_OK
+
+
+def test_full_loop_32x16x1_matches_oracle(mmlib):
+    w, prob, oprob = small_film(mmlib)
+    F = w.fields()
+    mavg_ref, res_ref, _ = om.sweep(oprob, w.initial_m(), F, om.Demag(oprob), tol=w.tol)
+    m = dev(w.initial_m())
+    st, mavg, res = mmlib.mm_hysteresis_sweep(prob, m, F, opts=mmlib.make_opts(tol=w.tol))
+    assert st == mmlib.MM_OK and all(r.converged for r in res)
+    a, b = om.loop_metrics(F, mavg), om.loop_metrics(F, mavg_ref)
+    step = np.linalg.norm(F[0] - F[1])
+    assert abs(a["H_sw"] - b["H_sw"]) <= step * (1 + 1e-9)
+    assert abs(a["M_r"] - b["M_r"]) <= 1e-3
+    evals = sum(r.heff_evals for r in res)
+    evals_ref = sum(r.heff_evals for r in res_ref)
+    assert abs(evals - evals_ref) <= 0.2 * evals_ref
+    # away from switching events (jumps of <m> in either loop, +-3 field
+    # values) the loops agree per field value
+    jumps = np.zeros(len(F), bool)
+    for mv in (mavg, mavg_ref):
+        d = np.linalg.norm(np.diff(mv, axis=0), axis=1) > 0.02
+        jumps[1:] |= d
+    near = np.zeros(len(F), bool)
+    for i in np.nonzero(jumps)[0]:
+        near[max(0, i - 3): i + 4] = True
+    assert np.count_nonzero(~near) > len(F) // 2
+    diff = np.max(np.abs(mavg - mavg_ref), axis=1)
+    assert np.max(diff[~near]) < 1e-3, [(i, diff[i]) for i in np.nonzero((diff > 1e-3) & ~near)[0]]
+
+
+def test_sweep_resume_equals_single_sweep(mmlib):
+    w, prob, oprob = small_film(mmlib)
+    F = w.fields()[:40]
+    m1 = dev(w.initial_m())
+    _, mavg1, _ = mmlib.mm_hysteresis_sweep(prob, m1, F, opts=mmlib.make_opts(tol=w.tol))
+    m2 = dev(w.initial_m())
+    mavg2 = np.full((40, 3), np.nan)
+    mmlib.mm_hysteresis_sweep(prob, m2, F[:17], opts=mmlib.make_opts(tol=w.tol), mavg=mavg2[:17])
+    _, mavg2, _ = mmlib.mm_hysteresis_sweep(prob, m2, F, start=17, opts=mmlib.make_opts(tol=w.tol), mavg=mavg2)
+    assert np.array_equal(mavg1, mavg2)
+    assert torch.equal(m1, m2)
