@@ -162,14 +162,34 @@ def algorithmic_model(info, esz):
     }
 
 
+def kernel_source_hash():
+    """sha256 (first 16 hex) of the CUDA sources, to tell whether a committed
+    ncu summary still describes the kernels that run."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1405_2728_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def load_traffic(stage, workload, precision):
-    """dram bytes per launch from the committed ncu summary, if one matches."""
-    path = os.path.join(ROOT, "profiles", f"traffic_{workload}_{precision}.json")
+    """DRAM bytes per launch of a stage from the committed ncu summary
+    (profiles/ncu_<workload>_<precision>.md), or None when there is none or the
+    kernels changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", f"ncu_{workload}_{precision}.md")
     try:
-        with open(path) as f:
-            return json.load(f).get(stage)
-    except (OSError, ValueError):
+        text = open(path).read()
+    except OSError:
         return None
+    if f"`{kernel_source_hash()}`" not in text:
+        return None
+    for line in text.splitlines():
+        parts = line.split()
+        if len(parts) == 3 and parts[0] == "traffic_bytes_per_launch" and parts[1] == stage:
+            return int(parts[2])
+    return None
 
 
 def oracle_rate(w, seconds_budget=15.0, max_evals=40):
@@ -234,6 +254,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--workload", default="film_512x256x4")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-stages", type=int, default=0,
+                    help="only set up the workload and launch each kernel stage this many times (for ncu)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -265,6 +287,11 @@ def main():
     stream = torch.cuda.current_stream(dev)
     m = torch.from_numpy(w.initial_m()).to(device=dev, dtype=tdt).contiguous()
     flush = torch.empty(int(256 * 2**20) // 4, dtype=torch.float32, device=dev)  # > 2x L2
+
+    if args.profile_stages > 0:
+        print(json.dumps(mm.mm_kernel_times(prob, m, F[0], reps=args.profile_stages, stream=stream)))
+        prob.close()
+        return 0
 
     def field_step(buf, i):
         st, _, res = mm.mm_hysteresis_sweep(prob, buf, F[: i + 1], start=i, opts=opts, stream=stream)

@@ -84,6 +84,14 @@ __global__ void __launch_bounds__(768) k_xfwd(Geom g, FieldPtrs<T> P)
                     m0 = (a * m0 - tau * g0) * inv;
                     m1 = (a * m1 - tau * g1) * inv;
                     m2 = (a * m2 - tau * g2) * inv;
+                    if (sizeof(T) == 4) {
+                        // float path only: the closed form keeps |m| = 1 exactly in
+                        // exact arithmetic; in float its rounding drifts ~1e-7 per
+                        // step, so the float path renormalises (the double path keeps
+                        // the pure midpoint form, drift ~1e-16 per step)
+                        const T r = rsqrtf((float)(m0 * m0 + m1 * m1 + m2 * m2));
+                        m0 *= r; m1 *= r; m2 *= r;
+                    }
                 } else {
                     m0 -= tau * g0; m1 -= tau * g1; m2 -= tau * g2;
                     const T inv = (T)1 / sqrt(m0 * m0 + m1 * m1 + m2 * m2);

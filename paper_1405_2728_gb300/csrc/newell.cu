@@ -223,3 +223,4 @@ int mm_tensor_spectrum(mm_problem *p, const double *N_dev, cudaStream_t s)
     if (e) { mm_set_cuda_error(e, "tensor spectrum"); return MM_ERR_CUDA; }
     return MM_OK;
 }
+
