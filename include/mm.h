@@ -106,6 +106,28 @@ typedef struct {
 MM_API int mm_newell(const mm_grid *grid, double *N_out, void *stream);
 
 /*
+ * mm_newell_static -- the same tensor as mm_newell, for callers that cannot
+ * allocate device memory.  The paper has no counterpart; this call exists for
+ * callers whose device memory is fully reserved by another allocator or
+ * capped by a fixed budget, and for code on latency-critical streams that must
+ * not call cudaMalloc/cudaFree (which may synchronise the whole device).
+ * It calls no allocating routine: its double-double work table is a static
+ * device array of 6 MiB compiled into the library, held by every GPU that
+ * loads it until the process exits.
+ * N_dev: DEVICE memory only (host pointers return MM_ERR_ARG), double,
+ * [6][nz][ny][nx], same layout and values as mm_newell.
+ * Limit: (nx+1)(ny+1)(nz+1) <= 65536 lattice points (e.g. 255 x 127 x 1,
+ * 63 x 63 x 15); larger grids return MM_ERR_UNSUPPORTED and launch nothing.
+ * Asynchronous on `stream`; returns after launching (launch errors give
+ * MM_ERR_CUDA).  The first call on each device looks up the table's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls on a device share the one table:
+ * calls whose kernels overlap on the GPU (different streams without ordering)
+ * race and give wrong results.
+ */
+MM_API int mm_newell_static(const mm_grid *grid, double *N_dev, void *stream);
+
+/*
  * mm_setup_geometry -- create a problem: validates the grid and material,
  * allocates device workspaces, computes the Newell tensor (as mm_newell), its
  * Fourier spectrum on the zero-padded grid (padded size per axis: the smallest

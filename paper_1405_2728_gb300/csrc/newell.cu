@@ -224,3 +224,71 @@ int mm_tensor_spectrum(mm_problem *p, const double *N_dev, cudaStream_t s)
     return MM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// mm_newell_static: the Newell tensor without any device allocation.
+//
+// Some callers cannot allocate device memory: a process whose memory is
+// fully reserved up front by another allocator (a framework's caching pool
+// or a fixed per-process budget), or code on a latency-critical stream where
+// cudaMalloc/cudaFree, which can synchronise the whole device, are not
+// allowed.  For them the double-double table of f and g lives in this
+// file-scope device array instead of a cudaMallocAsync buffer.  The array is
+// part of the library's image, so every GPU that loads libmmgb.so holds it
+// (6 MiB) until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+#define MM_NEWELL_STATIC_POINTS 65536L  // (nx+1)(ny+1)(nz+1) lattice points, six dd values each
+
+static __device__ __align__(256) dd_t g_newell_static_table[6 * MM_NEWELL_STATIC_POINTS];
+
+namespace {
+std::mutex g_static_mutex;
+void *g_static_addr[256];  // device address of the table, per device ordinal
+}
+
+extern "C" MM_API int mm_newell_static(const mm_grid *gr, double *N_dev, void *stream)
+{
+    if (!gr || !N_dev || gr->nx < 1 || gr->ny < 1 || gr->nz < 1 || !(gr->dx > 0) || !(gr->dy > 0) ||
+        !(gr->dz > 0) || !isfinite(gr->dx) || !isfinite(gr->dy) || !isfinite(gr->dz))
+        return MM_ERR_ARG;
+    const long na = (long)(gr->nx + 1) * (gr->ny + 1) * (gr->nz + 1);
+    if (na > MM_NEWELL_STATIC_POINTS) return MM_ERR_UNSUPPORTED;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, N_dev) != cudaSuccess) { cudaGetLastError(); return MM_ERR_ARG; }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return MM_ERR_ARG;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e) { mm_set_cuda_error(e, "cudaGetDevice"); return MM_ERR_CUDA; }
+    if (dev < 0 || dev >= 256) return MM_ERR_UNSUPPORTED;
+    dd_t *T = nullptr;
+    {
+        // first call on this device: look up the device address of the table
+        // (in host code the array's name is only a host-side stand-in)
+        std::lock_guard<std::mutex> lk(g_static_mutex);
+        if (!g_static_addr[dev]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_newell_static_table);
+            if (e) { mm_set_cuda_error(e, "cudaGetSymbolAddress"); return MM_ERR_CUDA; }
+            g_static_addr[dev] = p;
+        }
+        T = static_cast<dd_t *>(g_static_addr[dev]);
+    }
+    double h = gr->dx;
+    if (gr->dy > h) h = gr->dy;
+    if (gr->dz > h) h = gr->dz;
+    const double hx = gr->dx / h, hy = gr->dy / h, hz = gr->dz / h;
+    const long nn = (long)gr->nx * gr->ny * gr->nz;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int bt = 128;
+    long blocks = (na + bt - 1) / bt;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    // every table entry read by the stencil is written first, so nothing needs clearing
+    k_newell_table<<<(int)blocks, bt, 0, s>>>(gr->nx, gr->ny, gr->nz, hx, hy, hz, T);
+    blocks = (nn + bt - 1) / bt;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    k_newell_stencil<<<(int)blocks, bt, 0, s>>>(gr->nx, gr->ny, gr->nz, hx, hy, hz, T, N_dev);
+    e = cudaGetLastError();
+    if (e) { mm_set_cuda_error(e, "mm_newell_static kernels"); return MM_ERR_CUDA; }
+    return MM_OK;
+}

@@ -75,6 +75,7 @@ def lib():
         L = ctypes.CDLL(LIB_PATH)
         dp = POINTER(c_double)
         L.mm_newell.argtypes = [POINTER(mm_grid), c_void_p, c_void_p]
+        L.mm_newell_static.argtypes = [POINTER(mm_grid), c_void_p, c_void_p]
         L.mm_setup_geometry.argtypes = [POINTER(mm_grid), POINTER(mm_material), c_int, c_void_p, POINTER(c_void_p)]
         L.mm_destroy.argtypes = [c_void_p]
         L.mm_heff.argtypes = [c_void_p, c_void_p, dp, c_void_p, c_void_p]
@@ -87,7 +88,7 @@ def lib():
         L.mm_status_string.argtypes = [c_int]
         L.mm_status_string.restype = c_char_p
         L.mm_last_cuda_error.restype = c_char_p
-        for name in ("mm_newell", "mm_setup_geometry", "mm_destroy", "mm_heff", "mm_energy", "mm_minimize",
+        for name in ("mm_newell", "mm_newell_static", "mm_setup_geometry", "mm_destroy", "mm_heff", "mm_energy", "mm_minimize",
                      "mm_hysteresis_sweep", "mm_problem_info", "mm_kernel_times"):
             getattr(L, name).restype = c_int
         _lib = L
@@ -195,6 +196,16 @@ def mm_newell(grid: mm_grid, N_out, stream=None):
     """Newell tensor octant into N_out (6, nz, ny, nx) float64 (host or device)."""
     _check(lib().mm_newell(ctypes.byref(grid), _ptr(N_out, np.float64, (6, grid.nz, grid.ny, grid.nx), "N_out"),
                            _stream(stream, N_out)), "mm_newell")
+    return N_out
+
+
+def mm_newell_static(grid: mm_grid, N_out, stream=None):
+    """As mm_newell, without device allocation: N_out must be a CUDA tensor
+    (6, nz, ny, nx) float64; asynchronous on the stream; grids up to
+    (nx+1)(ny+1)(nz+1) <= 65536 lattice points."""
+    _check(lib().mm_newell_static(ctypes.byref(grid),
+                                  _ptr(N_out, np.float64, (6, grid.nz, grid.ny, grid.nx), "N_out"),
+                                  _stream(stream, N_out)), "mm_newell_static")
     return N_out
 
 
