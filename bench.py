@@ -115,7 +115,7 @@ def algorithmic_model(info, esz):
     Bytes: compulsory traffic of the pass structure -- xfwd reads m_k and g_k
     and writes m_{k+1} and the x-spectrum; yz reads/writes the spectrum and
     reads the tensor spectra; xinv reads the spectrum, m_{k+1}, m_k and g_k and
-    writes g_{k+1}.  Flops: real arithmetic of the radix-8 Stockham transforms
+    writes g_{k+1} (its last CTA also sums the per-CTA partials and picks tau).  Flops: real arithmetic of the radix-8 Stockham transforms
     with zero-padding pruning, the tensor product and the local terms."""
     nx, ny, nz, Px, Py, Pz = (info[k] for k in ("nx", "ny", "nz", "px", "py", "pz"))
     N = nx * ny * nz
@@ -151,14 +151,13 @@ def algorithmic_model(info, esz):
     x_rows = 3 * ny * nz
     unpack = 10 * C
     f_xfwd = x_rows * (fft_flops(Hx, True, False) + unpack) + N * 3 * 8
-    f_xinv = x_rows * (fft_flops(Hx, False, True) + unpack) + N * 3 * 40
+    f_xinv = x_rows * (fft_flops(Hx, False, True) + unpack) + N * 90
     zf = 3 * (fft_flops(Pz, True, False) + fft_flops(Pz, False, False))
     f_yz = C * (3 * nz * (fft_flops(Py, True, False) + fft_flops(Py, False, True)) + Py * (zf + Pz * 36))
     return {
         "xfwd_step": {"bytes": 3 * F + W, "flops": f_xfwd},
         "yz_conv": {"bytes": 2 * W + T, "flops": f_yz},
-        "xinv_local": {"bytes": W + 4 * F, "flops": f_xinv},
-        "reduce_bb": {"bytes": 0, "flops": 0},
+        "xinv_local_bb": {"bytes": W + 4 * F, "flops": f_xinv},
     }
 
 
@@ -190,6 +189,21 @@ def load_traffic(stage, workload, precision):
         if len(parts) == 3 and parts[0] == "traffic_bytes_per_launch" and parts[1] == stage:
             return int(parts[2])
     return None
+
+
+def combine_ranks(evals, ms, e2e_evals, e2e_ms, ws, device):
+    """Whole-job figures of independent replicas: evaluations summed over the
+    ranks, times taken from the slowest rank (max), for both legs."""
+    if ws <= 1:
+        return float(evals), float(ms), float(e2e_evals), float(e2e_ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(evals), float(ms), float(e2e_evals), float(e2e_ms)], dtype=torch.float64, device=device)
+    s = t.clone()
+    dist.all_reduce(s, op=dist.ReduceOp.SUM)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    return s[0].item(), mx[1].item(), s[2].item(), mx[3].item()
 
 
 def oracle_rate(w, seconds_budget=15.0, max_evals=40):
@@ -345,13 +359,7 @@ def main():
     ktimes = mm.mm_kernel_times(prob, m, F[args.warmup], reps=30, stream=stream)
     model = algorithmic_model(info, esz)
 
-    tot = torch.tensor([float(evals), ms, float(e2e_evals), e2e_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        s = tot.clone(); dist.all_reduce(s, op=dist.ReduceOp.SUM)
-        mx = tot.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        evals_all, ms_max, e2e_all, e2e_max = s[0].item(), mx[1].item(), s[2].item(), mx[3].item()
-    else:
-        evals_all, ms_max, e2e_all, e2e_max = evals, ms, e2e_evals, e2e_ms
+    evals_all, ms_max, e2e_all, e2e_max = combine_ranks(evals, ms, e2e_evals, e2e_ms, ws, dev)
     if rank != 0:
         dist.destroy_process_group() if ws > 1 else None
         return 0

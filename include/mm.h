@@ -131,8 +131,9 @@ MM_API int mm_newell_static(const mm_grid *grid, double *N_dev, void *stream);
  * mm_setup_geometry -- create a problem: validates the grid and material,
  * allocates device workspaces, computes the Newell tensor (as mm_newell), its
  * Fourier spectrum on the zero-padded grid (padded size per axis: the smallest
- * power of two >= 2n-1, and >= 2 along x), and captures the minimiser's CUDA
- * graph.  precision = MM_FP64 or MM_FP32: element type of m/H and of the FFT
+ * power of two >= 2n-1, and >= 2 along x), times the admissible launch
+ * shapes of the field kernels on this problem and keeps the fastest, and
+ * captures the minimiser's CUDA graph.  precision = MM_FP64 or MM_FP32: element type of m/H and of the FFT
  * and stencil arithmetic; reductions (step sizes, energies, averages) are
  * always accumulated in double.
  * Supported in this build (else MM_ERR_UNSUPPORTED): nx <= 2048 (padded x
@@ -241,6 +242,8 @@ typedef struct {
     long workspace_bytes;      /* device memory owned by the problem */
     long spectrum_bytes;       /* one padded field spectrum (3 components, x-half) */
     long tensor_bytes;         /* stored tensor spectra */
+    int x_tile_rows;           /* launch shape picked by the setup autotuner: y rows per x-kernel CTA */
+    int yz_batch_rows;         /* ... and y rows transformed together in the y-z kernel */
 } mm_info;
 MM_API int mm_problem_info(const mm_problem *prob, mm_info *info);
 

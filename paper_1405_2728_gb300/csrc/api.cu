@@ -9,6 +9,17 @@
 #include <new>
 
 #include "common.cuh"
+#include "fft.cuh"
+#include <nvtx3/nvToolsExt.h>
+
+namespace {
+// NVTX range around each entry point (a no-op unless a profiler is attached);
+// lets profilers select e.g. the kernels of mm_kernel_times only.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+}
 
 // implemented in heff.cu
 int mm_launch_field(mm_problem *p, const void *m, void *H, const double *hext, int mode, cudaStream_t s);
@@ -85,7 +96,7 @@ void free_problem(mm_problem *p)
     if (p->graph) cudaGraphDestroy(p->graph);
     void *bufs[] = {p->mbuf[0], p->mbuf[1], p->gbuf[0], p->gbuf[1], p->W, p->Nhat, p->tw_px, p->tw_py,
                     p->tw_pz, p->Kc, p->uc, p->partials, p->st, p->Hext_dev, p->stage_in, p->stage_out,
-                    p->rec_dev};
+                    p->rec_dev, p->counter};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (p->st_host) cudaFreeHost(p->st_host);
@@ -113,21 +124,33 @@ int plan(mm_problem *p)
     g.can = 2.0 / (MM_MU0 * p->mat.Ms);
     g.K = p->mat.K;
     g.u[0] = p->mat.u[0]; g.u[1] = p->mat.u[1]; g.u[2] = p->mat.u[2];
-    const size_t vsz = p->precision == MM_FP64 ? 16 : 8;
     if (g.Px > 4096 || g.Pz > 8) return MM_ERR_UNSUPPORTED;
-    if (3 * g.nz * g.Gy > 768) return MM_ERR_UNSUPPORTED;
-    // row strides: one complex of padding to spread rows over the banks
-    g.rsx = g.Hx + 1;
-    g.rsy = g.Py + 1;
-    if ((size_t)3 * g.nz * g.rsy * vsz > 200 * 1024) return MM_ERR_UNSUPPORTED;
-    // rows per x tile: as many as fit in 768 threads and ~100 KiB, power of two, <= ny
-    int ty = 1;
-    while (ty * 2 <= 16 && 3 * (ty * 2) * g.Gx <= 768 && (size_t)3 * (ty * 2) * g.rsx * vsz <= 100 * 1024 &&
-           ty * 2 <= next_pow2(gr.ny))
-        ty *= 2;
-    g.TY = ty;
-    if (3 * g.TY * g.Gx > 768) return MM_ERR_UNSUPPORTED;
-    p->nblk_x = ((gr.ny + g.TY - 1) / g.TY) * gr.nz;
+    // padded shared-memory rows (one pad element per 8, see fft.cuh)
+    g.rsx = padded_row(g.Hx);
+    g.rsy = padded_row(g.Py);
+    if (g.rsx <= g.Hx || g.rsy <= g.Py) return MM_ERR_UNSUPPORTED;  // the kernels index rows with these strides
+    // admissible launch shapes; mm_autotune picks among them after setup
+    const size_t smax = 200 * 1024;
+    {
+        // y rows per batch in the y-z kernel: divisors of 3 nz with RB*Gy
+        // threads within the kernel's bound
+        const int maxT = mm_yz_thread_bound(p), nrow = 3 * g.nz;
+        p->nrb = 0;
+        for (int rb = nrow; rb >= 1 && p->nrb < 16; --rb)
+            if (nrow % rb == 0 && rb * g.Gy <= maxT) p->rbs[p->nrb++] = rb;
+        if (!p->nrb) return MM_ERR_UNSUPPORTED;
+        g.RB = p->rbs[0];
+        if (mm_smem_yz_for(p) > smax) return MM_ERR_UNSUPPORTED;
+    }
+    // y rows per CTA in the x kernels: powers of two up to 16 (and up to the
+    // next power of two of ny) within 768 threads and the shared-memory cap
+    p->nty = 0;
+    for (int ty = 1; ty <= 16 && ty <= next_pow2(gr.ny); ty *= 2)
+        if (3 * ty * g.Gx <= 768 && mm_smem_x_for(p, ty) <= smax) p->tys[p->nty++] = ty;
+    if (!p->nty) return MM_ERR_UNSUPPORTED;
+    g.TY = p->tys[p->nty - 1];
+    // partial sums are sized for the smallest tile (most CTAs)
+    p->nblk_x = ((gr.ny + p->tys[0] - 1) / p->tys[0]) * gr.nz;
     return MM_OK;
 }
 
@@ -196,6 +219,7 @@ int status_of(int s)
 
 extern "C" int mm_newell(const mm_grid *grid, double *N_out, void *stream)
 {
+    NvtxRange nvtx_("mm_newell");
     if (!grid_ok(grid) || !N_out) return MM_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t bytes = sizeof(double) * 6 * (size_t)grid->nx * grid->ny * grid->nz;
@@ -216,6 +240,7 @@ extern "C" int mm_newell(const mm_grid *grid, double *N_out, void *stream)
 extern "C" int mm_setup_geometry(const mm_grid *grid, const mm_material *mat, int precision, void *stream,
                                  mm_problem **out)
 {
+    NvtxRange nvtx_("mm_setup_geometry");
     if (!out || !grid_ok(grid) || !mat) return MM_ERR_ARG;
     if (precision != MM_FP64 && precision != MM_FP32) return MM_ERR_ARG;
     if (!(std::isfinite(mat->Ms) && mat->Ms > 0) || !(std::isfinite(mat->A) && mat->A >= 0) || !std::isfinite(mat->K))
@@ -249,11 +274,12 @@ extern "C" int mm_setup_geometry(const mm_grid *grid, const mm_material *mat, in
             (rc = dalloc(p, &p->tw_pz, g.Pz * vsz)) ||
             (rc = dalloc(p, (void **)&p->partials, sizeof(double) * RED_NSLOT * (size_t)p->nblk_x)) ||
             (rc = dalloc(p, (void **)&p->st, sizeof(MinState))) ||
+            (rc = dalloc(p, (void **)&p->counter, 64)) ||
             (rc = dalloc(p, (void **)&p->Hext_dev, 4 * sizeof(double))) ||
             (rc = dalloc(p, &p->stage_in, F)) || (rc = dalloc(p, &p->stage_out, F)))
             break;
         if (cudaMallocHost((void **)&p->st_host, sizeof(MinState))) { rc = MM_ERR_OOM; break; }
-        if (cudaMemsetAsync(p->st, 0, sizeof(MinState), s) || cudaMemsetAsync(p->gbuf[0], 0, F, s) ||
+        if (cudaMemsetAsync(p->st, 0, sizeof(MinState), s) || cudaMemsetAsync(p->counter, 0, 64, s) || cudaMemsetAsync(p->gbuf[0], 0, F, s) ||
             cudaMemsetAsync(p->gbuf[1], 0, F, s)) { rc = MM_ERR_CUDA; break; }
         // per-cell material, converted to the working precision
         if (mat->K_cell || mat->u_cell) {
@@ -282,7 +308,12 @@ extern "C" int mm_setup_geometry(const mm_grid *grid, const mm_material *mat, in
         cudaFree(Nd);
         if (rc != MM_OK) break;
         if (e) { mm_set_cuda_error(e, "setup"); rc = MM_ERR_CUDA; break; }
-        if ((rc = mm_heff_configure(p)) != MM_OK) break;
+        if ((rc = mm_heff_configure(p, mm_smem_x_for(p, p->tys[p->nty - 1]))) != MM_OK) break;
+        if (cudaMemsetAsync(p->mbuf[0], 0, F, s)) { rc = MM_ERR_CUDA; break; }
+        {
+            NvtxRange nvtx_tune("mm_autotune");
+            if ((rc = mm_autotune(p, p->tys, p->nty, p->rbs, p->nrb, s)) != MM_OK) break;
+        }
         if ((rc = build_graph(p)) != MM_OK) break;
     } while (0);
     if (rc != MM_OK) {
@@ -313,6 +344,8 @@ extern "C" int mm_problem_info(const mm_problem *p, mm_info *info)
     info->workspace_bytes = p->bytes;
     info->spectrum_bytes = (long)g.C * 3 * g.nz * g.ny * 2 * (long)p->esz;
     info->tensor_bytes = (long)g.C * (g.Pz / 2 + 1) * (g.Py / 2 + 1) * 6 * (long)p->esz;
+    info->x_tile_rows = g.TY;
+    info->yz_batch_rows = g.RB;
     return MM_OK;
 }
 
@@ -343,12 +376,14 @@ static int field_call(mm_problem *p, const void *m, const double Hext[3], void *
 
 extern "C" int mm_heff(mm_problem *p, const void *m, const double Hext[3], void *H_out, void *stream)
 {
+    NvtxRange nvtx_("mm_heff");
     if (!p || !m || !H_out || !vec_ok(Hext)) return MM_ERR_ARG;
     return field_call(p, m, Hext, H_out, MODE_HEFF, (cudaStream_t)stream);
 }
 
 extern "C" int mm_energy(mm_problem *p, const void *m, const double Hext[3], double E_out[5], void *stream)
 {
+    NvtxRange nvtx_("mm_energy");
     if (!p || !m || !E_out || !vec_ok(Hext)) return MM_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     int rc = field_call(p, m, Hext, nullptr, MODE_ENERGY, s);
@@ -373,6 +408,7 @@ static void fill_result(const MinState &st, mm_min_result *r, long extra_launche
 extern "C" int mm_minimize(mm_problem *p, void *m, const double Hext[3], const mm_min_opts *opts,
                            mm_min_result *res, void *stream)
 {
+    NvtxRange nvtx_("mm_minimize");
     if (!p || !m || !vec_ok(Hext) || !opts_ok(opts)) return MM_ERR_ARG;
     if (!p->graph_ready) return MM_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
@@ -394,6 +430,7 @@ extern "C" int mm_minimize(mm_problem *p, void *m, const double Hext[3], const m
 extern "C" int mm_hysteresis_sweep(mm_problem *p, void *m, const double *H_list, int n, int start,
                                    const mm_min_opts *opts, double *mavg, mm_min_result *per_step, void *stream)
 {
+    NvtxRange nvtx_("mm_hysteresis_sweep");
     if (!p || !m || !H_list || !mavg || n < 1 || start < 0 || start >= n || !opts_ok(opts)) return MM_ERR_ARG;
     for (int i = start; i < n; ++i)
         if (!vec_ok(H_list + 3 * i)) return MM_ERR_ARG;
@@ -441,6 +478,7 @@ extern "C" int mm_hysteresis_sweep(mm_problem *p, void *m, const double *H_list,
 extern "C" int mm_kernel_times(mm_problem *p, const void *m, const double Hext[3], int reps, double *ms_out,
                                const char **names, int *count, void *stream)
 {
+    NvtxRange nvtx_("mm_kernel_times");
     if (!p || !m || !vec_ok(Hext) || reps < 1 || !ms_out || !names || !count) return MM_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t F = 3 * (size_t)p->g.N * p->esz;

@@ -88,6 +88,7 @@ struct Geom {
     int lhx, lpy;          // log2(Hx), log2(Py)
     int Gx, Gy;            // threads per FFT row: max(1, L/8)
     int TY;                // y rows per CTA in the x kernels
+    int RB;                // y rows transformed at once in the y-z kernel (divides 3 nz)
     int rsx, rsy;          // smem row strides (complex elements) of the x and y FFT rows
     long N;                // cells
     double dx, dy, dz;
@@ -108,7 +109,7 @@ struct FieldPtrs {
     T *H_out;              // MODE_HEFF output
     T *mbuf[2];            // minimiser iterate buffers
     T *gbuf[2];            // projected-gradient buffers
-    V *W;                  // spectrum [C][3][nz][ny]
+    V *W;                  // spectrum [C][nz][ny][3] (x-frequency slowest, component fastest)
     const T *Nhat;         // tensor spectra [C][Pz/2+1][Py/2+1][6], scaled by -Ms/(Px Py Pz)
     const V *tw_px;        // exp(-2 pi i t/Px), t < Px
     const V *tw_py;        // exp(-2 pi i t/Py), t < Py
@@ -117,7 +118,7 @@ struct FieldPtrs {
     const T *uc;           // per-cell axis [3][N] or NULL
     double *partials;      // [nblocks][RED_NSLOT]
     MinState *st;          // minimiser state (MODE_MIN and updates)
-    const double *Hext;    // device copy of H_ext for MODE_HEFF/ENERGY (or st->Hext)
+    unsigned *counter;     // CTAs of the current x-inverse launch that have finished (reset by the last)
 };
 
 // ---------------------------------------------------------------------------
@@ -136,7 +137,10 @@ struct mm_problem {
     void *tw_px, *tw_py, *tw_pz;
     void *Kc, *uc;
     double *partials;
+    unsigned *counter;     // completion counter of the x-inverse kernel
     int nblk_x;            // CTAs of the x kernels (= partial slots)
+    int tys[8], nty;       // admissible rows-per-tile of the x kernels
+    int rbs[16], nrb;      // admissible rows-per-batch of the y-z kernel
     MinState *st;
     MinState *st_host;     // pinned mirror
     double *Hext_dev;
@@ -158,9 +162,11 @@ int mm_kernel_stage_times(mm_problem *p, int reps, double *ms, const char **name
 int mm_launch_init_state(mm_problem *p, const double Hext[3], const mm_min_opts *o, int reset_base, cudaStream_t s);
 int mm_launch_record(mm_problem *p, int step, cudaStream_t s);
 int mm_launch_copy_result(mm_problem *p, void *dst, cudaStream_t s);
-size_t mm_smem_x(const mm_problem *p);
-size_t mm_smem_yz(const mm_problem *p);
-int mm_heff_configure(mm_problem *p);
+size_t mm_smem_x_for(const mm_problem *p, int ty);
+size_t mm_smem_yz_for(const mm_problem *p);
+int mm_yz_thread_bound(const mm_problem *p);
+int mm_heff_configure(mm_problem *p, size_t sx_max);
+int mm_autotune(mm_problem *p, const int *tys, int nty, const int *rbs, int nrb, cudaStream_t s);
 int mm_launch_twiddles(mm_problem *p, cudaStream_t s);
 // implemented in newell.cu
 int mm_newell_device(const mm_grid *g, double *N_dev, cudaStream_t s);

@@ -21,6 +21,14 @@
 
 template <typename V> __device__ __forceinline__ V czero() { V r; r.x = 0; r.y = 0; return r; }
 
+// Rows in shared memory are stored with one padding element after every 8:
+// element i lives at pidx(i).  Stockham stores of radix 8 and strides 1 or 8
+// then spread over all banks instead of hitting one bank group.
+__host__ __device__ __forceinline__ int pidx(int i) { return i + (i >> 3); }
+// shared-memory footprint (elements) of a padded row of length L, plus one
+// element so that consecutive rows start in different banks
+__host__ __device__ __forceinline__ int padded_row(int L) { return L + (L >> 3) + 1; }
+
 // 2-point DFT
 template <bool HIN, typename V> __device__ __forceinline__ void dft2(V &a0, V &a1)
 {
@@ -97,31 +105,35 @@ __device__ __forceinline__ void stockham_pass(V *row, int L, int Ns, int j, int 
     constexpr int NB = 8 / R;
     V v[8];
     const int LR = L / R;
+    if (active) {
 #pragma unroll
-    for (int q = 0; q < NB && active; ++q) {
-        const int b = j + q * G;
+        for (int q = 0; q < NB; ++q) {
+            const int b = j + q * G;
 #pragma unroll
-        for (int r = 0; r < R; ++r)
-            v[q * R + r] = (HIN && r >= R / 2) ? czero<V>() : row[b + r * LR];
-        if (Ns > 1) {
-            const int k = b & (Ns - 1);
-            const int step = (L / (Ns * R)) * k * ts;
+            for (int r = 0; r < R; ++r)
+                v[q * R + r] = (HIN && r >= R / 2) ? czero<V>() : row[pidx(b + r * LR)];
+            if (Ns > 1) {
+                const int k = b & (Ns - 1);
+                const int step = (L / (Ns * R)) * k * ts;
 #pragma unroll
-            for (int r = 1; r < R; ++r) {
-                const V w = tw[r * step];
-                v[q * R + r] = INV ? cmulc(v[q * R + r], w) : cmul(v[q * R + r], w);
+                for (int r = 1; r < R; ++r) {
+                    const V w = tw[r * step];
+                    v[q * R + r] = INV ? cmulc(v[q * R + r], w) : cmul(v[q * R + r], w);
+                }
             }
+            dftR<R, INV, HIN>(&v[q * R]);
         }
-        dftR<R, INV, HIN>(&v[q * R]);
     }
     __syncthreads();
+    if (active) {
 #pragma unroll
-    for (int q = 0; q < NB && active; ++q) {
-        const int b = j + q * G;
-        const int k = b & (Ns - 1);
-        const int base = (b - k) * R + k;
+        for (int q = 0; q < NB; ++q) {
+            const int b = j + q * G;
+            const int k = b & (Ns - 1);
+            const int base = (b - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < (HOUT ? R / 2 : R); ++r) row[base + r * Ns] = v[q * R + r];
+            for (int r = 0; r < (HOUT ? R / 2 : R); ++r) row[pidx(base + r * Ns)] = v[q * R + r];
+        }
     }
     __syncthreads();
 }
@@ -134,7 +146,7 @@ __device__ __forceinline__ void stockham_pass(V *row, int L, int Ns, int j, int 
 // synchronises before the call so that the row's contents are visible; the
 // row is final after return.
 template <bool INV, bool HIN, bool HOUT, typename V>
-__device__ void fft_row(V *row, int L, int logL, int j, const V *__restrict__ tw, int ts, bool active)
+__device__ __forceinline__ void fft_row(V *row, int L, int logL, int j, const V *__restrict__ tw, int ts, bool active)
 {
     if (L == 1) return;
     if (L < 8) {

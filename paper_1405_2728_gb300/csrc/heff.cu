@@ -1,14 +1,14 @@
 // Effective-field and minimiser-step kernels (sm_103a).
 //
 // One evaluation of H_eff (Eq. effective_field; Sections 3 and 4) is three
-// kernels over the zero-padded grid, and the minimiser (Section 2) adds a
-// one-CTA reduction kernel:
+// kernels over the zero-padded grid; in the minimiser (Section 2) the last of
+// them also finishes the iteration:
 //
 //  k_xfwd     per (z, tile of TY rows): optional minimiser step (the closed
 //             form of the midpoint scheme, Eq. implicit_gradient_descent, or
 //             the renormalised explicit step) fused with the real-to-complex
 //             FFT along x of the three components, zero padding nx -> Px,
-//             written transposed to the spectrum W[kx][c][z][y].
+//             written transposed to the spectrum W[kx][z][y][c].
 //  k_yz       per x-frequency kx: FFT along y (padding ny -> Py) in shared
 //             memory, then per ky in registers FFT along z, the product with
 //             the symmetric 3x3 tensor spectrum (H^ = -Ms N^ m^, normalisation
@@ -17,13 +17,17 @@
 //  k_xinv     per (z, tile): complex-to-real inverse FFT along x keeping nx
 //             values, then the local terms: exchange (six-point stencil, free
 //             faces), uniaxial anisotropy, Zeeman.  Depending on the mode it
-//             writes H, or accumulates energies, or forms the projected
+//             writes H, or accumulates the energy terms, or forms the projected
 //             gradient g = m x (m x H) (Eq. projected_direction) with the
 //             Barzilai-Borwein sums s.s, s.y, y.y (Eq. stepsize), max |m x H|,
-//             energies and sum m, in double, one partial set per CTA.
-//  k_reduce   one CTA: fixed-order sum of the partials, step size tau^1 / tau^2
-//             alternating (Eq. stepsize), stop rule, and the device-side loop
-//             condition of the CUDA graph.
+//             the energy and sum m.  Each CTA stores its partial sums; the last
+//             CTA to finish sums them in a fixed order (deterministic), picks
+//             the step size tau^1 / tau^2 alternately (Eq. stepsize), applies
+//             the stop rule and sets the device-side loop condition.
+//
+// Sums are accumulated in double on the double path and in compensated
+// float pairs (TwoSum, Knuth) on the float path, and always combined across
+// CTAs in double.
 #include <cstdio>
 
 #include "common.cuh"
@@ -32,6 +36,37 @@
 namespace {
 
 template <typename T> __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
+
+// real element x of a padded complex row holding Px reals
+template <typename T, typename V> __device__ __forceinline__ T &rel(V *row, int x)
+{
+    return reinterpret_cast<T *>(row + pidx(x >> 1))[x & 1];
+}
+
+// v * W^n (forward) or v * W^-n (inverse), W = exp(-2 pi i / PZ), n < PZ/2,
+// with the constants of PZ = 4 and PZ = 8 written out
+template <int PZ, bool INV, typename V> __device__ __forceinline__ V tw_pz(V v, int n)
+{
+    typedef decltype(v.x) T;
+    const T r = (T)0.70710678118654752440084436210484903928;
+    if (n == 0 || PZ <= 2) return v;
+    if (PZ == 4 || (PZ == 8 && n == 2)) return cmul_mi<INV>(v);  // W^1 of PZ = 4, W^2 of PZ = 8: -i
+    V o;
+    if (n == 1) {
+        if (INV) { o.x = r * (v.x - v.y); o.y = r * (v.x + v.y); }
+        else { o.x = r * (v.x + v.y); o.y = r * (v.y - v.x); }
+    } else {  // PZ == 8, n == 3
+        if (INV) { o.x = -r * (v.x + v.y); o.y = r * (v.x - v.y); }
+        else { o.x = r * (v.y - v.x); o.y = -r * (v.x + v.y); }
+    }
+    return o;
+}
+
+// copy a twiddle table of n complex values into shared memory
+template <typename V> __device__ __forceinline__ void load_twiddles(V *dst, const V *src, int n)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
 
 // ---------------------------------------------------------------------------
 // k_xfwd
@@ -46,6 +81,8 @@ __global__ void __launch_bounds__(768) k_xfwd(Geom g, FieldPtrs<T> P)
     const int TY = g.TY, y0 = blockIdx.x * TY, z = blockIdx.y;
     const int nx = g.nx, ny = g.ny, Px = g.Px;
     const long N = g.N;
+    V *tw = S + 3 * TY * g.rsx;  // Px twiddles exp(-2 pi i t / Px)
+    load_twiddles(tw, P.tw_px, Px);
 
     const T *src;
     T *dst = nullptr;
@@ -57,19 +94,19 @@ __global__ void __launch_bounds__(768) k_xfwd(Geom g, FieldPtrs<T> P)
         const long k = st->k;
         const int cur = st->base ^ (int)(k & 1);
         if (k > 0) {
-            src = P.mbuf[cur ^ 1];
-            dst = P.mbuf[cur];
-            gp = P.gbuf[(int)((k - 1) & 1)];
+            src = cur ? P.mbuf[0] : P.mbuf[1];
+            dst = cur ? P.mbuf[1] : P.mbuf[0];
+            gp = ((k - 1) & 1) ? P.gbuf[1] : P.gbuf[0];
             tau = (T)st->tau;
             step_kind = st->step_kind;
         } else {
-            src = P.mbuf[cur];
+            src = cur ? P.mbuf[1] : P.mbuf[0];
         }
     } else {
         src = P.m_src;
     }
 
-    // load (and step) the tile, write reals into the rows: row (c, yl) holds Px reals
+    // load (and step) the tile; row (c, yl) holds Px reals
     for (int e = tid; e < TY * nx; e += nth) {
         const int yl = e / nx, x = e - yl * nx, y = y0 + yl;
         T m0 = 0, m1 = 0, m2 = 0;
@@ -100,15 +137,14 @@ __global__ void __launch_bounds__(768) k_xfwd(Geom g, FieldPtrs<T> P)
                 dst[n] = m0; dst[N + n] = m1; dst[2 * N + n] = m2;
             }
         }
-        T *r0 = reinterpret_cast<T *>(S + (0 * TY + yl) * g.rsx);
-        T *r1 = reinterpret_cast<T *>(S + (1 * TY + yl) * g.rsx);
-        T *r2 = reinterpret_cast<T *>(S + (2 * TY + yl) * g.rsx);
-        r0[x] = m0; r1[x] = m1; r2[x] = m2;
+        rel<T>(S + (0 * TY + yl) * g.rsx, x) = m0;
+        rel<T>(S + (1 * TY + yl) * g.rsx, x) = m1;
+        rel<T>(S + (2 * TY + yl) * g.rsx, x) = m2;
     }
     const int npad = Px - nx;
     for (int e = tid; e < 3 * TY * npad; e += nth) {
         const int row = e / npad, x = nx + (e - row * npad);
-        reinterpret_cast<T *>(S + row * g.rsx)[x] = 0;
+        rel<T>(S + row * g.rsx, x) = 0;
     }
     __syncthreads();
 
@@ -116,33 +152,37 @@ __global__ void __launch_bounds__(768) k_xfwd(Geom g, FieldPtrs<T> P)
     {
         const int row = tid / g.Gx, j = tid - row * g.Gx;
         const bool act = row < 3 * TY;
-        fft_row<false, true, false>(S + (act ? row : 0) * g.rsx, g.Hx, g.lhx, j, P.tw_px, 2, act);
+        fft_row<false, true, false>(S + (act ? row : 0) * g.rsx, g.Hx, g.lhx, j, tw, 2, act);
     }
 
     // unpack to the real-input spectrum X[k], k = 0..Hx, and store transposed
     const int Hx = g.Hx, C = g.C;
     for (int e = tid; e < TY * 3 * C; e += nth) {
-        const int yl = e % TY, rest = e / TY, c = rest % 3, k = rest / 3;
+        const int c = e % 3, rest = e / 3, yl = rest % TY, k = rest / TY;
         const int y = y0 + yl;
         const V *row = S + (c * TY + yl) * g.rsx;
-        const V Zk = row[k == Hx ? 0 : k];
-        const V Zm = cconj(row[k == 0 ? 0 : Hx - k]);
-        const V w = P.tw_px[k];
+        const V Zk = row[pidx(k == Hx ? 0 : k)];
+        const V Zm = cconj(row[pidx(k == 0 ? 0 : Hx - k)]);
+        const V w = tw[k];
         const V sum = cadd(Zk, Zm), dif = csub(Zk, Zm);
         // X = (sum - i w dif) / 2
         const V wd = cmul(w, dif);
         V X;
         X.x = (T)0.5 * (sum.x + wd.y);
         X.y = (T)0.5 * (sum.y - wd.x);
-        if (y < ny) P.W[(((long)k * 3 + c) * g.nz + z) * ny + y] = X;
+        if (y < ny) P.W[(((long)k * g.nz + z) * ny + y) * 3 + c] = X;
     }
 }
 
 // ---------------------------------------------------------------------------
 // k_yz
 // ---------------------------------------------------------------------------
+// the double kernel runs fewer, fatter threads (its z-phase keeps ~100
+// doubles live); the y rows are then transformed in batches of RB rows
+template <typename T> struct YZBound { static constexpr int v = sizeof(T) == 8 ? 512 : 768; };
+
 template <typename T, int PZ>
-__global__ void __launch_bounds__(768) k_yz(Geom g, FieldPtrs<T> P)
+__global__ void __launch_bounds__(YZBound<T>::v) k_yz(Geom g, FieldPtrs<T> P)
 {
     typedef typename cvec<T>::type V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -152,218 +192,135 @@ __global__ void __launch_bounds__(768) k_yz(Geom g, FieldPtrs<T> P)
     const int ny = g.ny, nz = g.nz, Py = g.Py;
     const int nrow = 3 * nz;
     V *Wk = P.W + (long)kx * nrow * ny;
+    V *tw = S + nrow * g.rsy;  // Py twiddles
+    load_twiddles(tw, P.tw_py, Py);
 
-    for (int e = tid; e < nrow * ny; e += nth) {
-        const int row = e / ny, y = e - row * ny;
-        S[row * g.rsy + y] = Wk[e];
+    for (int e = tid; e < nrow * ny; e += nth) {  // Wk[z][y][c] -> row (c, z)
+        const int c = e % 3, rest = e / 3, zz = rest / ny, y = rest - zz * ny;
+        S[(c * nz + zz) * g.rsy + pidx(y)] = Wk[e];
     }
     const int npad = Py - ny;
     for (int e = tid; e < nrow * npad; e += nth) {
         const int row = e / npad, y = ny + (e - row * npad);
-        S[row * g.rsy + y] = czero<V>();
+        S[row * g.rsy + pidx(y)] = czero<V>();
     }
     __syncthreads();
-    const int row = tid / g.Gy, j = tid - row * g.Gy;
-    const bool act = row < nrow;
-    V *myrow = S + (act ? row : 0) * g.rsy;
-    fft_row<false, true, false>(myrow, Py, g.lpy, j, P.tw_py, 1, act);
+    const int rb = tid / g.Gy, j = tid - rb * g.Gy;  // row within a batch of g.RB rows
+    const bool act = rb < g.RB;
+    for (int r0 = 0; r0 < nrow; r0 += g.RB)
+        fft_row<false, true, false>(S + (act ? r0 + rb : 0) * g.rsy, Py, g.lpy, j, tw, 1, act);
 
-    // per ky: z transform, tensor product, inverse z transform
+    // per ky: z transform, tensor product, inverse z transform.  The z input
+    // has nz <= PZ/2 non-zero values and only nz outputs are kept, so the
+    // PZ-point transforms split into their even and odd frequencies:
+    //   X[2k+h] = DFT_{PZ/2}(x[n] W^{nh})[k],  W = exp(-2 pi i/PZ),
+    //   y[z]    = IDFT_{PZ/2}(H_even)[z] + W^{-z} IDFT_{PZ/2}(H_odd)[z],
+    // and each half is done in turn to keep fewer values live.
+    constexpr int HZ = PZ > 1 ? PZ / 2 : 1;
     const int hy = Py / 2, hz = PZ / 2;
     const T *Nk = P.Nhat + (long)kx * (hz + 1) * (hy + 1) * 6;
     for (int ky = tid; ky < Py; ky += nth) {
-        V a[3][PZ];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-#pragma unroll
-            for (int zz = 0; zz < PZ; ++zz)
-                a[c][zz] = (zz < nz) ? S[(c * nz + zz) * g.rsy + ky] : czero<V>();
-            if (PZ > 1) dft_small<PZ, false, true>(a[c]);
-        }
+        const int pky = pidx(ky);
         const int kyr = ky <= hy ? ky : Py - ky;
         const T sy = ky <= hy ? (T)1 : (T)-1;
+        V out[3][HZ];
 #pragma unroll
-        for (int kz = 0; kz < PZ; ++kz) {
-            const int kzr = kz <= hz ? kz : PZ - kz;
-            const T sz = kz <= hz ? (T)1 : (T)-1;
-            const T *n6 = Nk + ((long)kzr * (hy + 1) + kyr) * 6;
-            const T nxx = ldg(n6 + 0), nyy = ldg(n6 + 1), nzz = ldg(n6 + 2);
-            const T nxy = sy * ldg(n6 + 3), nxz = sz * ldg(n6 + 4), nyz = sy * sz * ldg(n6 + 5);
-            const V m0 = a[0][kz], m1 = a[1][kz], m2 = a[2][kz];
-            V h0, h1, h2;
-            h0.x = nxx * m0.x + nxy * m1.x + nxz * m2.x; h0.y = nxx * m0.y + nxy * m1.y + nxz * m2.y;
-            h1.x = nxy * m0.x + nyy * m1.x + nyz * m2.x; h1.y = nxy * m0.y + nyy * m1.y + nyz * m2.y;
-            h2.x = nxz * m0.x + nyz * m1.x + nzz * m2.x; h2.y = nxz * m0.y + nyz * m1.y + nzz * m2.y;
-            a[0][kz] = h0; a[1][kz] = h1; a[2][kz] = h2;
+        for (int half = 0; half < (PZ > 1 ? 2 : 1); ++half) {
+            V b[3][HZ];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+#pragma unroll
+                for (int n = 0; n < HZ; ++n) {
+                    const V x = (n < nz) ? S[(c * nz + n) * g.rsy + pky] : czero<V>();
+                    b[c][n] = half ? tw_pz<PZ, false>(x, n) : x;
+                }
+                dft_small<HZ, false, false>(b[c]);
+            }
+#pragma unroll
+            for (int kh = 0; kh < HZ; ++kh) {
+                const int kz = PZ > 1 ? 2 * kh + half : 0;
+                const int kzr = kz <= hz ? kz : PZ - kz;
+                const T sz = kz <= hz ? (T)1 : (T)-1;
+                const T *n6 = Nk + ((long)kzr * (hy + 1) + kyr) * 6;
+                const T nxx = ldg(n6 + 0), nyy = ldg(n6 + 1), nzz = ldg(n6 + 2);
+                const T nxy = sy * ldg(n6 + 3), nxz = sz * ldg(n6 + 4), nyz = sy * sz * ldg(n6 + 5);
+                const V m0 = b[0][kh], m1 = b[1][kh], m2 = b[2][kh];
+                V h0, h1, h2;
+                h0.x = nxx * m0.x + nxy * m1.x + nxz * m2.x; h0.y = nxx * m0.y + nxy * m1.y + nxz * m2.y;
+                h1.x = nxy * m0.x + nyy * m1.x + nyz * m2.x; h1.y = nxy * m0.y + nyy * m1.y + nyz * m2.y;
+                h2.x = nxz * m0.x + nyz * m1.x + nzz * m2.x; h2.y = nxz * m0.y + nyz * m1.y + nzz * m2.y;
+                b[0][kh] = h0; b[1][kh] = h1; b[2][kh] = h2;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                dft_small<HZ, true, false>(b[c]);
+#pragma unroll
+                for (int n = 0; n < HZ; ++n) {
+                    if (half == 0) out[c][n] = b[c][n];
+                    else out[c][n] = cadd(out[c][n], tw_pz<PZ, true>(b[c][n], n));
+                }
+            }
         }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            if (PZ > 1) dft_small<PZ, true, false>(a[c]);
+        for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int zz = 0; zz < PZ; ++zz)
-                if (zz < nz) S[(c * nz + zz) * g.rsy + ky] = a[c][zz];
-        }
+            for (int zz = 0; zz < HZ; ++zz)
+                if (zz < nz) S[(c * nz + zz) * g.rsy + pky] = out[c][zz];
     }
     __syncthreads();
-    fft_row<true, false, true>(myrow, Py, g.lpy, j, P.tw_py, 1, act);
+    for (int r0 = 0; r0 < nrow; r0 += g.RB)
+        fft_row<true, false, true>(S + (act ? r0 + rb : 0) * g.rsy, Py, g.lpy, j, tw, 1, act);
 
     for (int e = tid; e < nrow * ny; e += nth) {
-        const int r = e / ny, y = e - r * ny;
-        Wk[e] = S[r * g.rsy + y];
+        const int c = e % 3, rest = e / 3, zz = rest / ny, y = rest - zz * ny;
+        Wk[e] = S[(c * nz + zz) * g.rsy + pidx(y)];
     }
 }
 
 // ---------------------------------------------------------------------------
-// block reduction of RED_NSLOT doubles (sum, except the max slot)
+// reductions
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void block_reduce_store(double *v, double *scratch, double *out)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int s = 0; s < RED_NSLOT; ++s) {
-        double x = v[s];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double y = __shfl_down_sync(0xffffffffu, x, o);
-            x = (s == RED_T2MAX) ? fmax(x, y) : x + y;
-        }
-        if (lane == 0) scratch[warp * RED_NSLOT + s] = x;
-    }
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int s = 0; s < RED_NSLOT; ++s) {
-            double x = lane < nw ? scratch[lane * RED_NSLOT + s] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const double y = __shfl_down_sync(0xffffffffu, x, o);
-                x = (s == RED_T2MAX) ? fmax(x, y) : x + y;
-            }
-            if (lane == 0) out[s] = x;
-        }
-    }
-}
+// Slots of the per-CTA partial sums.  In MODE_MIN: s.s, s.y, y.y,
+// max |m x H|^2, energy density sum, sum m.  In MODE_ENERGY: m.H_demag,
+// m.H_exchange, K(1 - (m.u)^2), m.H_ext, -, sum m.
+enum { SL_SS = 0, SL_SY = 1, SL_YY = 2, SL_T2 = 3, SL_ET = 4, SL_MX = 5, SL_MY = 6, SL_MZ = 7, NSL = 8 };
+enum { SL_ED = 0, SL_EEX = 1, SL_EAN = 2, SL_EZ = 3 };
+static_assert(NSL <= RED_NSLOT, "partials buffer holds RED_NSLOT doubles per CTA");
 
-// ---------------------------------------------------------------------------
-// k_xinv
-// ---------------------------------------------------------------------------
-template <typename T, int MODE>
-__global__ void __launch_bounds__(768) k_xinv(Geom g, FieldPtrs<T> P, double hx0, double hx1, double hx2)
-{
-    typedef typename cvec<T>::type V;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    V *S = reinterpret_cast<V *>(smem_raw);
-    const int tid = threadIdx.x, nth = blockDim.x;
-    const int TY = g.TY, y0 = blockIdx.x * TY, z = blockIdx.y;
-    const int nx = g.nx, ny = g.ny, nz = g.nz, Hx = g.Hx;
-    const long N = g.N;
-
-    // complex-to-real preprocessing: Z[k] = (X[k] + X*[Hx-k]) + i conj(w^k) (X[k] - X*[Hx-k])
-    for (int e = tid; e < TY * 3 * Hx; e += nth) {
-        const int yl = e % TY, rest = e / TY, c = rest % 3, k = rest / 3;
-        const int y = y0 + yl;
-        V Z = czero<V>();
-        if (y < ny) {
-            const long base = ((long)c * nz + z) * ny + y;
-            const long strideK = (long)3 * nz * ny;
-            const V Xk = P.W[(long)k * strideK + base];
-            const V Xm = cconj(P.W[(long)(Hx - k) * strideK + base]);
-            const V sum = cadd(Xk, Xm), dif = csub(Xk, Xm);
-            const V t = cmulc(dif, P.tw_px[k]);  // conj(w^k) dif
-            Z.x = sum.x - t.y;
-            Z.y = sum.y + t.x;
-        }
-        S[(c * TY + yl) * g.rsx + k] = Z;
-    }
-    __syncthreads();
+// accumulator: double on the double path, a compensated float pair on the float path
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+    double v;
+    __device__ __forceinline__ void zero() { v = 0.0; }
+    __device__ __forceinline__ void add(double x) { v += x; }
+    __device__ __forceinline__ void add(const Acc &o) { v += o.v; }
+    __device__ __forceinline__ void maxv(double x) { v = fmax(v, x); }
+    __device__ __forceinline__ void maxv(const Acc &o) { v = fmax(v, o.v); }
+    __device__ __forceinline__ Acc shfl_down(int o) const { Acc r; r.v = __shfl_down_sync(0xffffffffu, v, o); return r; }
+    __device__ __forceinline__ double value() const { return v; }
+};
+template <> struct Acc<float> {
+    float hi, lo;
+    __device__ __forceinline__ void zero() { hi = 0.f; lo = 0.f; }
+    __device__ __forceinline__ void add(float x)
     {
-        const int row = tid / g.Gx, j = tid - row * g.Gx;
-        const bool act = row < 3 * TY;
-        fft_row<true, false, true>(S + (act ? row : 0) * g.rsx, Hx, g.lhx, j, P.tw_px, 2, act);
+        const float s = hi + x, bb = s - hi;
+        lo += (hi - (s - bb)) + (x - bb);
+        hi = s;
     }
-
-    // local terms
-    const MinState *st = P.st;
-    long k = 0;
-    int cur = 0;
-    const T *m;
-    if (MODE == MODE_MIN) {
-        k = st->k;
-        cur = st->base ^ (int)(k & 1);
-        m = P.mbuf[cur];
-        hx0 = st->Hext[0]; hx1 = st->Hext[1]; hx2 = st->Hext[2];
-    } else {
-        m = P.m_src;
+    __device__ __forceinline__ void add(const Acc &o) { add(o.hi); lo += o.lo; }
+    __device__ __forceinline__ void maxv(float x) { hi = fmaxf(hi, x); }
+    __device__ __forceinline__ void maxv(const Acc &o) { hi = fmaxf(hi, o.hi); }
+    __device__ __forceinline__ Acc shfl_down(int o) const
+    {
+        Acc r;
+        r.hi = __shfl_down_sync(0xffffffffu, hi, o);
+        r.lo = __shfl_down_sync(0xffffffffu, lo, o);
+        return r;
     }
-    const T he0 = (T)hx0, he1 = (T)hx1, he2 = (T)hx2;
-    const T cx = (T)g.cex_x, cy = (T)g.cex_y, cz = (T)g.cex_z, can = (T)g.can;
-    double red[RED_NSLOT];
-#pragma unroll
-    for (int s = 0; s < RED_NSLOT; ++s) red[s] = 0.0;
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
 
-    for (int e = tid; e < TY * nx; e += nth) {
-        const int yl = e / nx, x = e - yl * nx, y = y0 + yl;
-        if (y >= ny) continue;
-        const long n = ((long)z * ny + y) * nx + x;
-        const T d0 = reinterpret_cast<const T *>(S + (0 * TY + yl) * g.rsx)[x];
-        const T d1 = reinterpret_cast<const T *>(S + (1 * TY + yl) * g.rsx)[x];
-        const T d2 = reinterpret_cast<const T *>(S + (2 * TY + yl) * g.rsx)[x];
-        const T m0 = m[n], m1 = m[N + n], m2 = m[2 * N + n];
-        // exchange: sum over present neighbours of (m_j - m_i) / d^2 (free faces)
-        T e0 = 0, e1 = 0, e2 = 0;
-        if (x > 0)      { e0 += cx * (m[n - 1] - m0);  e1 += cx * (m[N + n - 1] - m1);  e2 += cx * (m[2 * N + n - 1] - m2); }
-        if (x < nx - 1) { e0 += cx * (m[n + 1] - m0);  e1 += cx * (m[N + n + 1] - m1);  e2 += cx * (m[2 * N + n + 1] - m2); }
-        if (y > 0)      { e0 += cy * (m[n - nx] - m0); e1 += cy * (m[N + n - nx] - m1); e2 += cy * (m[2 * N + n - nx] - m2); }
-        if (y < ny - 1) { e0 += cy * (m[n + nx] - m0); e1 += cy * (m[N + n + nx] - m1); e2 += cy * (m[2 * N + n + nx] - m2); }
-        const long sxy = (long)nx * ny;
-        if (z > 0)      { e0 += cz * (m[n - sxy] - m0); e1 += cz * (m[N + n - sxy] - m1); e2 += cz * (m[2 * N + n - sxy] - m2); }
-        if (z < nz - 1) { e0 += cz * (m[n + sxy] - m0); e1 += cz * (m[N + n + sxy] - m1); e2 += cz * (m[2 * N + n + sxy] - m2); }
-        // uniaxial anisotropy
-        const T Kv = P.Kc ? P.Kc[n] : (T)g.K;
-        T u0, u1, u2;
-        if (P.uc) { u0 = P.uc[n]; u1 = P.uc[N + n]; u2 = P.uc[2 * N + n]; }
-        else { u0 = (T)g.u[0]; u1 = (T)g.u[1]; u2 = (T)g.u[2]; }
-        const T mu = m0 * u0 + m1 * u1 + m2 * u2;
-        const T ka = can * Kv * mu;
-        const T H0 = d0 + e0 + ka * u0 + he0;
-        const T H1 = d1 + e1 + ka * u1 + he1;
-        const T H2 = d2 + e2 + ka * u2 + he2;
-        if (MODE == MODE_HEFF) {
-            P.H_out[n] = H0; P.H_out[N + n] = H1; P.H_out[2 * N + n] = H2;
-            continue;
-        }
-        red[RED_ED] += (double)(m0 * d0 + m1 * d1 + m2 * d2);
-        red[RED_EEX] += (double)(m0 * e0 + m1 * e1 + m2 * e2);
-        red[RED_EAN] += (double)(Kv * ((T)1 - mu * mu));
-        red[RED_EZ] += (double)(m0 * he0 + m1 * he1 + m2 * he2);
-        red[RED_MX] += (double)m0; red[RED_MY] += (double)m1; red[RED_MZ] += (double)m2;
-        if (MODE == MODE_MIN) {
-            // a = m x H, g = m x a = m x (m x H)
-            const T a0 = m1 * H2 - m2 * H1, a1 = m2 * H0 - m0 * H2, a2 = m0 * H1 - m1 * H0;
-            const T g0 = m1 * a2 - m2 * a1, g1 = m2 * a0 - m0 * a2, g2 = m0 * a1 - m1 * a0;
-            red[RED_T2MAX] = fmax(red[RED_T2MAX], (double)(a0 * a0 + a1 * a1 + a2 * a2));
-            T *gout = P.gbuf[(int)(k & 1)];
-            if (k > 0) {
-                const T *mp = P.mbuf[cur ^ 1];
-                const T *gq = P.gbuf[(int)((k - 1) & 1)];  // g_{k-1}
-                const T s0 = m0 - mp[n], s1 = m1 - mp[N + n], s2 = m2 - mp[2 * N + n];
-                const T y0v = g0 - gq[n], y1v = g1 - gq[N + n], y2v = g2 - gq[2 * N + n];
-                red[RED_SS] += (double)(s0 * s0 + s1 * s1 + s2 * s2);
-                red[RED_SY] += (double)(s0 * y0v + s1 * y1v + s2 * y2v);
-                red[RED_YY] += (double)(y0v * y0v + y1v * y1v + y2v * y2v);
-            }
-            gout[n] = g0; gout[N + n] = g1; gout[2 * N + n] = g2;
-        }
-    }
-    if (MODE == MODE_HEFF) return;
-    __syncthreads();  // the FFT rows are no longer needed: reuse shared memory as scratch
-    double *scratch = reinterpret_cast<double *>(smem_raw);
-    block_reduce_store(red, scratch, P.partials + (long)(blockIdx.y * gridDim.x + blockIdx.x) * RED_NSLOT);
-}
-
-// ---------------------------------------------------------------------------
-// k_reduce: one CTA
-// ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long globaltimer_ns()
 {
     unsigned long long t;
@@ -371,47 +328,52 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
     return t;
 }
 
+// Last CTA of the field evaluation: sum the per-CTA partials in block order
+// (one warp; fixed order, so the result does not depend on which CTA came
+// last), then finish the iteration on lane 0.
 template <int MODE>
-__global__ void __launch_bounds__(256) k_reduce(const double *partials, int nblk, MinState *st, Geom g,
-                                                cudaGraphConditionalHandle h, int use_cond, int body_kernels)
+__device__ void finish_iteration(const Geom &g, double *partials, int nblk, MinState *st,
+                                 cudaGraphConditionalHandle h, int use_cond, int body_kernels)
 {
-    __shared__ double scratch[8 * RED_NSLOT];
-    __shared__ double tot[RED_NSLOT];
-    double v[RED_NSLOT];
+    const int lane = threadIdx.x & 31;
+    double tot[NSL];
 #pragma unroll
-    for (int s = 0; s < RED_NSLOT; ++s) v[s] = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-#pragma unroll
-        for (int s = 0; s < RED_NSLOT; ++s) {
-            const double x = partials[(long)b * RED_NSLOT + s];
-            v[s] = (s == RED_T2MAX) ? fmax(v[s], x) : v[s] + x;
+    for (int s = 0; s < NSL; ++s) {
+        const bool isMax = (MODE == MODE_MIN && s == SL_T2);
+        double v = 0.0;
+        for (int b = lane; b < nblk; b += 32) {
+            const double x = __ldcg(partials + (long)b * RED_NSLOT + s);
+            v = isMax ? fmax(v, x) : v + x;
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double y = __shfl_down_sync(0xffffffffu, v, o);
+            v = isMax ? fmax(v, y) : v + y;
+        }
+        tot[s] = v;
     }
-    block_reduce_store(v, scratch, tot);
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-
-    const double V = g.dx * g.dy * g.dz, Ms = g.Ms;
-    const double Ed = -0.5 * MM_MU0 * Ms * V * tot[RED_ED];
-    const double Eex = -0.5 * MM_MU0 * Ms * V * tot[RED_EEX];
-    const double Ean = V * tot[RED_EAN];
-    const double Ez = -MM_MU0 * Ms * V * tot[RED_EZ];
-    st->energy[0] = Ed; st->energy[1] = Eex; st->energy[2] = Ean; st->energy[3] = Ez;
-    st->energy[4] = Ed + Eex + Ean + Ez;
-    st->mavg[0] = tot[RED_MX] / (double)g.N;
-    st->mavg[1] = tot[RED_MY] / (double)g.N;
-    st->mavg[2] = tot[RED_MZ] / (double)g.N;
-    if (MODE != MODE_MIN) return;
-
+    if (lane != 0) return;
+    const double V = g.dx * g.dy * g.dz, Ms = g.Ms, cE = MM_MU0 * Ms * V;
+    st->mavg[0] = tot[SL_MX] / (double)g.N;
+    st->mavg[1] = tot[SL_MY] / (double)g.N;
+    st->mavg[2] = tot[SL_MZ] / (double)g.N;
+    if (MODE == MODE_ENERGY) {
+        const double Ed = -0.5 * cE * tot[SL_ED], Eex = -0.5 * cE * tot[SL_EEX];
+        const double Ean = V * tot[SL_EAN], Ez = -cE * tot[SL_EZ];
+        st->energy[0] = Ed; st->energy[1] = Eex; st->energy[2] = Ean; st->energy[3] = Ez;
+        st->energy[4] = Ed + Eex + Ean + Ez;
+        return;
+    }
     const long k = st->k;
-    const double tmax = sqrt(tot[RED_T2MAX]);
+    const double tmax = sqrt(tot[SL_T2]);
     st->max_torque = tmax / Ms;
+    st->energy[4] = cE * tot[SL_ET];
     st->evals = k + 1;
     st->launches += body_kernels;
     if (k == 0) st->t_start_ns = globaltimer_ns();
     int stop = 1;
     const bool finite = isfinite(tmax) && isfinite(st->energy[4]) &&
-                        (k == 0 || (isfinite(tot[RED_SS]) && isfinite(tot[RED_SY]) && isfinite(tot[RED_YY])));
+                        (k == 0 || (isfinite(tot[SL_SS]) && isfinite(tot[SL_SY]) && isfinite(tot[SL_YY])));
     if (!finite) {
         st->status = MMS_NONFINITE;
     } else if (tmax < st->tol_abs) {
@@ -425,7 +387,7 @@ __global__ void __launch_bounds__(256) k_reduce(const double *partials, int nblk
         if (k == 0) {
             tau = st->tau0;
         } else {
-            const double ss = tot[RED_SS], sy = tot[RED_SY], yy = tot[RED_YY];
+            const double ss = tot[SL_SS], sy = tot[SL_SY], yy = tot[SL_YY];
             tau = (k & 1) ? ss / sy : sy / yy;
             if (!(isfinite(tau) && tau > 0.0)) tau = sqrt(ss / yy);
             if (!(isfinite(tau) && tau > 0.0)) tau = st->tau0;
@@ -437,6 +399,172 @@ __global__ void __launch_bounds__(256) k_reduce(const double *partials, int nblk
     if (use_cond) cudaGraphSetConditional(h, stop ? 0u : 1u);
 }
 
+// ---------------------------------------------------------------------------
+// k_xinv
+// ---------------------------------------------------------------------------
+template <typename T, int MODE>
+__global__ void __launch_bounds__(768) k_xinv(Geom g, FieldPtrs<T> P, double hx0, double hx1, double hx2,
+                                              cudaGraphConditionalHandle h, int use_cond)
+{
+    typedef typename cvec<T>::type V;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *S = reinterpret_cast<V *>(smem_raw);
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int TY = g.TY, y0 = blockIdx.x * TY, z = blockIdx.y;
+    const int nx = g.nx, ny = g.ny, nz = g.nz, Hx = g.Hx;
+    const long N = g.N;
+    V *tw = S + 3 * TY * g.rsx;
+    load_twiddles(tw, P.tw_px, g.Px);
+    __syncthreads();
+
+    // complex-to-real preprocessing: Z[k] = (X[k] + X*[Hx-k]) + i conj(w^k) (X[k] - X*[Hx-k])
+    for (int e = tid; e < TY * 3 * Hx; e += nth) {
+        const int c = e % 3, rest = e / 3, yl = rest % TY, k = rest / TY;
+        const int y = y0 + yl;
+        V Z = czero<V>();
+        if (y < ny) {
+            const long base = ((long)z * ny + y) * 3 + c;
+            const long strideK = (long)3 * nz * ny;
+            const V Xk = P.W[(long)k * strideK + base];
+            const V Xm = cconj(P.W[(long)(Hx - k) * strideK + base]);
+            const V sum = cadd(Xk, Xm), dif = csub(Xk, Xm);
+            const V t = cmulc(dif, tw[k]);  // conj(w^k) dif
+            Z.x = sum.x - t.y;
+            Z.y = sum.y + t.x;
+        }
+        S[(c * TY + yl) * g.rsx + pidx(k)] = Z;
+    }
+    __syncthreads();
+    {
+        const int row = tid / g.Gx, j = tid - row * g.Gx;
+        const bool act = row < 3 * TY;
+        fft_row<true, false, true>(S + (act ? row : 0) * g.rsx, Hx, g.lhx, j, tw, 2, act);
+    }
+
+    // local terms
+    MinState *st = P.st;
+    long k = 0;
+    int cur = 0;
+    const T *m;
+    if (MODE == MODE_MIN) {
+        k = st->k;
+        cur = st->base ^ (int)(k & 1);
+        m = cur ? P.mbuf[1] : P.mbuf[0];
+        hx0 = st->Hext[0]; hx1 = st->Hext[1]; hx2 = st->Hext[2];
+    } else {
+        m = P.m_src;
+    }
+    const T he0 = (T)hx0, he1 = (T)hx1, he2 = (T)hx2;
+    const T cx = (T)g.cex_x, cy = (T)g.cex_y, cz = (T)g.cex_z, can = (T)g.can;
+    const T kfac = (T)(0.5 * g.can);  // 1/(mu0 Ms)
+    const T Kuni = (T)g.K, ux = (T)g.u[0], uy = (T)g.u[1], uz = (T)g.u[2];  // converted once, not per cell
+    Acc<T> red[NSL];
+#pragma unroll
+    for (int s = 0; s < NSL; ++s) red[s].zero();
+
+    for (int e = tid; e < TY * nx; e += nth) {
+        const int yl = e / nx, x = e - yl * nx, y = y0 + yl;
+        if (y >= ny) continue;
+        const long n = ((long)z * ny + y) * nx + x;
+        const T d0 = rel<T>(S + (0 * TY + yl) * g.rsx, x);
+        const T d1 = rel<T>(S + (1 * TY + yl) * g.rsx, x);
+        const T d2 = rel<T>(S + (2 * TY + yl) * g.rsx, x);
+        const T m0 = m[n], m1 = m[N + n], m2 = m[2 * N + n];
+        // exchange: sum over present neighbours of (m_j - m_i) / d^2 (free faces)
+        T e0 = 0, e1 = 0, e2 = 0;
+        if (x > 0)      { e0 += cx * (m[n - 1] - m0);  e1 += cx * (m[N + n - 1] - m1);  e2 += cx * (m[2 * N + n - 1] - m2); }
+        if (x < nx - 1) { e0 += cx * (m[n + 1] - m0);  e1 += cx * (m[N + n + 1] - m1);  e2 += cx * (m[2 * N + n + 1] - m2); }
+        if (y > 0)      { e0 += cy * (m[n - nx] - m0); e1 += cy * (m[N + n - nx] - m1); e2 += cy * (m[2 * N + n - nx] - m2); }
+        if (y < ny - 1) { e0 += cy * (m[n + nx] - m0); e1 += cy * (m[N + n + nx] - m1); e2 += cy * (m[2 * N + n + nx] - m2); }
+        const long sxy = (long)nx * ny;
+        if (z > 0)      { e0 += cz * (m[n - sxy] - m0); e1 += cz * (m[N + n - sxy] - m1); e2 += cz * (m[2 * N + n - sxy] - m2); }
+        if (z < nz - 1) { e0 += cz * (m[n + sxy] - m0); e1 += cz * (m[N + n + sxy] - m1); e2 += cz * (m[2 * N + n + sxy] - m2); }
+        // uniaxial anisotropy
+        const T Kv = P.Kc ? P.Kc[n] : Kuni;
+        T u0, u1, u2;
+        if (P.uc) { u0 = P.uc[n]; u1 = P.uc[N + n]; u2 = P.uc[2 * N + n]; }
+        else { u0 = ux; u1 = uy; u2 = uz; }
+        const T mu = m0 * u0 + m1 * u1 + m2 * u2;
+        const T ka = can * Kv * mu;
+        const T H0 = d0 + e0 + ka * u0 + he0;
+        const T H1 = d1 + e1 + ka * u1 + he1;
+        const T H2 = d2 + e2 + ka * u2 + he2;
+        if (MODE == MODE_HEFF) {
+            P.H_out[n] = H0; P.H_out[N + n] = H1; P.H_out[2 * N + n] = H2;
+            continue;
+        }
+        red[SL_MX].add(m0); red[SL_MY].add(m1); red[SL_MZ].add(m2);
+        const T mhe = m0 * he0 + m1 * he1 + m2 * he2;
+        if (MODE == MODE_ENERGY) {
+            red[SL_ED].add(m0 * d0 + m1 * d1 + m2 * d2);
+            red[SL_EEX].add(m0 * e0 + m1 * e1 + m2 * e2);
+            red[SL_EAN].add(Kv * ((T)1 - mu * mu));
+            red[SL_EZ].add(mhe);
+            continue;
+        }
+        // projected gradient g = m x (m x H) = (m.H) m - |m|^2 H (the triple
+        // product identity; orthogonal to m for any |m|, which keeps the
+        // midpoint step norm-preserving even as rounding moves |m| off 1)
+        const T mh = m0 * H0 + m1 * H1 + m2 * H2;
+        const T mm = m0 * m0 + m1 * m1 + m2 * m2;
+        const T g0 = mh * m0 - mm * H0, g1 = mh * m1 - mm * H1, g2 = mh * m2 - mm * H2;
+        red[SL_T2].maxv(g0 * g0 + g1 * g1 + g2 * g2);  // |m x H|^2 = |g|^2 for |m| = 1
+        // energy density / (mu0 Ms V): -m.H/2 - m.H_ext/2 + K/(mu0 Ms)
+        red[SL_ET].add((T)-0.5 * (mh + mhe) + kfac * Kv);
+        T *gout = (k & 1) ? P.gbuf[1] : P.gbuf[0];
+        if (k > 0) {
+            const T *mp = cur ? P.mbuf[0] : P.mbuf[1];
+            const T *gq = (k & 1) ? P.gbuf[0] : P.gbuf[1];  // g_{k-1}
+            const T s0 = m0 - mp[n], s1 = m1 - mp[N + n], s2 = m2 - mp[2 * N + n];
+            const T y0v = g0 - gq[n], y1v = g1 - gq[N + n], y2v = g2 - gq[2 * N + n];
+            red[SL_SS].add(s0 * s0 + s1 * s1 + s2 * s2);
+            red[SL_SY].add(s0 * y0v + s1 * y1v + s2 * y2v);
+            red[SL_YY].add(y0v * y0v + y1v * y1v + y2v * y2v);
+        }
+        gout[n] = g0; gout[N + n] = g1; gout[2 * N + n] = g2;
+    }
+    if (MODE == MODE_HEFF) return;
+
+    // CTA reduction: the FFT rows are done with; stage every thread's
+    // accumulators in shared memory and let warp s reduce slot s.
+    __syncthreads();
+    Acc<T> *stage = reinterpret_cast<Acc<T> *>(smem_raw);
+#pragma unroll
+    for (int s = 0; s < NSL; ++s) stage[s * nth + tid] = red[s];
+    __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31;
+    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+    for (int s = warp; s < NSL; s += nth >> 5) {  // warp w reduces slots w, w + nwarps, ...
+        const bool isMax = (MODE == MODE_MIN && s == SL_T2);
+        Acc<T> a = stage[s * nth + lane];
+        for (int i = lane + 32; i < nth; i += 32) {
+            if (isMax) a.maxv(stage[s * nth + i]); else a.add(stage[s * nth + i]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const Acc<T> b = a.shfl_down(o);
+            if (isMax) a.maxv(b); else a.add(b);
+        }
+        if (lane == 0) P.partials[(long)bid * RED_NSLOT + s] = a.value();
+    }
+    // the last CTA to arrive finishes the evaluation
+    __shared__ int s_last;
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        const unsigned nblk = gridDim.x * gridDim.y;
+        s_last = (atomicAdd(P.counter, 1u) == nblk - 1);
+    }
+    __syncthreads();
+    if (!s_last || warp != 0) return;
+    __threadfence();
+    finish_iteration<MODE>(g, P.partials, gridDim.x * gridDim.y, st, h, use_cond, 3);
+    if (lane == 0) *P.counter = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------
 __global__ void k_init_state(MinState *st, double tau0, double tol_abs, double h0, double h1, double h2,
                              long max_iter, int step_kind, unsigned long long timeout_ns, int reset_base)
 {
@@ -501,24 +629,26 @@ template <typename T> FieldPtrs<T> make_ptrs(mm_problem *p)
     P.W = (V *)p->W; P.Nhat = (const T *)p->Nhat;
     P.tw_px = (const V *)p->tw_px; P.tw_py = (const V *)p->tw_py; P.tw_pz = (const V *)p->tw_pz;
     P.Kc = (const T *)p->Kc; P.uc = (const T *)p->uc;
-    P.partials = p->partials; P.st = p->st; P.Hext = nullptr;
+    P.partials = p->partials; P.st = p->st; P.counter = p->counter;
     return P;
-}
-
-template <typename T> size_t smem_x_t(const Geom &g)
-{
-    size_t b = (size_t)3 * g.TY * g.rsx * sizeof(typename cvec<T>::type);
-    size_t r = (size_t)32 * RED_NSLOT * sizeof(double);
-    return b > r ? b : r;
-}
-template <typename T> size_t smem_yz_t(const Geom &g)
-{
-    return (size_t)3 * g.nz * g.rsy * sizeof(typename cvec<T>::type);
 }
 
 static inline int round32(int n) { return (n + 31) & ~31; }
 template <typename T> int threads_x(const Geom &g) { return round32(3 * g.TY * g.Gx); }
-template <typename T> int threads_yz(const Geom &g) { return round32(3 * g.nz * g.Gy); }
+template <typename T> int threads_yz(const Geom &g) { return round32(g.RB * g.Gy); }
+
+template <typename T> size_t smem_x_t(const Geom &g)
+{
+    typedef typename cvec<T>::type V;
+    const size_t rows = (size_t)3 * g.TY * g.rsx * sizeof(V) + (size_t)g.Px * sizeof(V);
+    const size_t stage = (size_t)NSL * threads_x<T>(g) * sizeof(Acc<T>);
+    return rows > stage ? rows : stage;
+}
+template <typename T> size_t smem_yz_t(const Geom &g)
+{
+    typedef typename cvec<T>::type V;
+    return (size_t)3 * g.nz * g.rsy * sizeof(V) + (size_t)g.Py * sizeof(V);
+}
 
 template <typename T, int PZ>
 cudaError_t launch_yz(const Geom &g, const FieldPtrs<T> &P, cudaStream_t s)
@@ -544,22 +674,79 @@ template <typename T, int PZ> cudaError_t set_yz_attr(size_t smem)
     return cudaFuncSetAttribute(k_yz<T, PZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <typename T> cudaError_t configure_t(mm_problem *p)
+template <typename T> cudaError_t configure_t(size_t sx, size_t syz, int Pz)
 {
-    const size_t sx = smem_x_t<T>(p->g), syz = smem_yz_t<T>(p->g);
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_xfwd<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx))) return e;
     if ((e = cudaFuncSetAttribute(k_xfwd<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx))) return e;
     if ((e = cudaFuncSetAttribute(k_xinv<T, MODE_HEFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx))) return e;
     if ((e = cudaFuncSetAttribute(k_xinv<T, MODE_ENERGY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx))) return e;
     if ((e = cudaFuncSetAttribute(k_xinv<T, MODE_MIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx))) return e;
-    switch (p->g.Pz) {
+    switch (Pz) {
     case 1: return set_yz_attr<T, 1>(syz);
     case 2: return set_yz_attr<T, 2>(syz);
     case 4: return set_yz_attr<T, 4>(syz);
     case 8: return set_yz_attr<T, 8>(syz);
     }
     return cudaErrorInvalidValue;
+}
+
+// Launch-shape autotuner: time every admissible rows-per-tile TY of the x
+// kernels and rows-per-batch RB of the y-z kernel on this problem's own
+// buffers (three repetitions, best taken) and keep the fastest.  The
+// candidates are the ones mm_plan_candidates admitted.
+template <typename T> cudaError_t autotune_t(mm_problem *p, const int *tys, int nty, const int *rbs, int nrb,
+                                             cudaStream_t s)
+{
+    Geom g = p->g;
+    FieldPtrs<T> P = make_ptrs<T>(p);
+    P.m_src = (const T *)p->mbuf[0];
+    P.H_out = (T *)p->gbuf[0];
+    cudaEvent_t a, b;
+    cudaError_t e;
+    if ((e = cudaEventCreate(&a))) return e;
+    if ((e = cudaEventCreate(&b))) { cudaEventDestroy(a); return e; }
+    float best = 1e30f;
+    int bty = tys[0];
+    for (int i = 0; i < nty && !e; ++i) {
+        g.TY = tys[i];
+        const dim3 gx((g.ny + g.TY - 1) / g.TY, g.nz);
+        const size_t sx = smem_x_t<T>(g);
+        float tmin = 1e30f;
+        for (int r = 0; r < 3 && !e; ++r) {
+            cudaEventRecord(a, s);
+            k_xfwd<T, false><<<gx, threads_x<T>(g), sx, s>>>(g, P);
+            k_xinv<T, MODE_HEFF><<<gx, threads_x<T>(g), sx, s>>>(g, P, 0.0, 0.0, 0.0, 0, 0);
+            cudaEventRecord(b, s);
+            if ((e = cudaGetLastError()) || (e = cudaEventSynchronize(b))) break;
+            float t = 0;
+            cudaEventElapsedTime(&t, a, b);
+            if (t < tmin) tmin = t;
+        }
+        if (tmin < best) { best = tmin; bty = tys[i]; }
+    }
+    g.TY = bty;
+    best = 1e30f;
+    int brb = rbs[0];
+    for (int i = 0; i < nrb && !e; ++i) {
+        g.RB = rbs[i];
+        float tmin = 1e30f;
+        for (int r = 0; r < 3 && !e; ++r) {
+            cudaEventRecord(a, s);
+            e = launch_yz_any<T>(g, P, s);
+            cudaEventRecord(b, s);
+            if (e || (e = cudaEventSynchronize(b))) break;
+            float t = 0;
+            cudaEventElapsedTime(&t, a, b);
+            if (t < tmin) tmin = t;
+        }
+        if (tmin < best) { best = tmin; brb = rbs[i]; }
+    }
+    g.RB = brb;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (!e) p->g = g;
+    return e;
 }
 
 // Field chain for MODE_HEFF / MODE_ENERGY on caller-provided m (and H).
@@ -577,15 +764,10 @@ cudaError_t heff_chain_t(mm_problem *p, const void *m, void *H, const double *he
     if (e) return e;
     if ((e = launch_yz_any<T>(g, P, s))) return e;
     if (mode == MODE_HEFF)
-        k_xinv<T, MODE_HEFF><<<gx, threads_x<T>(g), sx, s>>>(g, P, hext[0], hext[1], hext[2]);
+        k_xinv<T, MODE_HEFF><<<gx, threads_x<T>(g), sx, s>>>(g, P, hext[0], hext[1], hext[2], 0, 0);
     else
-        k_xinv<T, MODE_ENERGY><<<gx, threads_x<T>(g), sx, s>>>(g, P, hext[0], hext[1], hext[2]);
-    if ((e = cudaGetLastError())) return e;
-    if (mode == MODE_ENERGY) {
-        k_reduce<MODE_ENERGY><<<1, 256, 0, s>>>(p->partials, p->nblk_x, p->st, g, 0, 0, 0);
-        e = cudaGetLastError();
-    }
-    return e;
+        k_xinv<T, MODE_ENERGY><<<gx, threads_x<T>(g), sx, s>>>(g, P, hext[0], hext[1], hext[2], 0, 0);
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -599,9 +781,7 @@ cudaError_t min_body_t(mm_problem *p, cudaGraphConditionalHandle h, cudaStream_t
     cudaError_t e = cudaGetLastError();
     if (e) return e;
     if ((e = launch_yz_any<T>(g, P, s))) return e;
-    k_xinv<T, MODE_MIN><<<gx, threads_x<T>(g), sx, s>>>(g, P, 0.0, 0.0, 0.0);
-    if ((e = cudaGetLastError())) return e;
-    k_reduce<MODE_MIN><<<1, 256, 0, s>>>(p->partials, p->nblk_x, p->st, g, h, use_cond, 4);
+    k_xinv<T, MODE_MIN><<<gx, threads_x<T>(g), sx, s>>>(g, P, 0.0, 0.0, 0.0, h, use_cond);
     return cudaGetLastError();
 }
 
@@ -612,10 +792,10 @@ cudaError_t stage_times_t(mm_problem *p, int reps, double *ms, cudaStream_t s)
     FieldPtrs<T> P = make_ptrs<T>(p);
     const dim3 gx((g.ny + g.TY - 1) / g.TY, g.nz);
     const size_t sx = smem_x_t<T>(g);
-    cudaEvent_t ev[5];
-    for (int i = 0; i < 5; ++i)
+    cudaEvent_t ev[4];
+    for (int i = 0; i < 4; ++i)
         if (cudaEventCreate(&ev[i])) return cudaGetLastError();
-    double acc[4] = {0, 0, 0, 0};
+    double acc[3] = {0, 0, 0};
     cudaError_t e = cudaSuccess;
     for (int r = 0; r < reps && !e; ++r) {
         cudaEventRecord(ev[0], s);
@@ -623,20 +803,18 @@ cudaError_t stage_times_t(mm_problem *p, int reps, double *ms, cudaStream_t s)
         cudaEventRecord(ev[1], s);
         launch_yz_any<T>(g, P, s);
         cudaEventRecord(ev[2], s);
-        k_xinv<T, MODE_MIN><<<gx, threads_x<T>(g), sx, s>>>(g, P, 0.0, 0.0, 0.0);
+        k_xinv<T, MODE_MIN><<<gx, threads_x<T>(g), sx, s>>>(g, P, 0.0, 0.0, 0.0, 0, 0);
         cudaEventRecord(ev[3], s);
-        k_reduce<MODE_MIN><<<1, 256, 0, s>>>(p->partials, p->nblk_x, p->st, g, 0, 0, 4);
-        cudaEventRecord(ev[4], s);
         if ((e = cudaGetLastError())) break;
-        if ((e = cudaEventSynchronize(ev[4]))) break;
-        for (int i = 0; i < 4; ++i) {
+        if ((e = cudaEventSynchronize(ev[3]))) break;
+        for (int i = 0; i < 3; ++i) {
             float t = 0;
             cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
             acc[i] += t;
         }
     }
-    for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
-    for (int i = 0; i < 4; ++i) ms[i] = acc[i] / (reps > 0 ? reps : 1);
+    for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+    for (int i = 0; i < 3; ++i) ms[i] = acc[i] / (reps > 0 ? reps : 1);
     return e;
 }
 
@@ -647,13 +825,33 @@ cudaError_t stage_times_t(mm_problem *p, int reps, double *ms, cudaStream_t s)
 // ---------------------------------------------------------------------------
 #define DISPATCH(p, expr_d, expr_f) ((p)->precision == MM_FP64 ? (expr_d) : (expr_f))
 
-size_t mm_smem_x(const mm_problem *p) { return DISPATCH(p, smem_x_t<double>(p->g), smem_x_t<float>(p->g)); }
-size_t mm_smem_yz(const mm_problem *p) { return DISPATCH(p, smem_yz_t<double>(p->g), smem_yz_t<float>(p->g)); }
 
-int mm_heff_configure(mm_problem *p)
+// Shared-memory needs of a launch shape (bytes), for the planner.
+size_t mm_smem_x_for(const mm_problem *p, int ty)
 {
-    cudaError_t e = DISPATCH(p, configure_t<double>(p), configure_t<float>(p));
+    Geom g = p->g;
+    g.TY = ty;
+    return DISPATCH(p, smem_x_t<double>(g), smem_x_t<float>(g));
+}
+size_t mm_smem_yz_for(const mm_problem *p)
+{
+    return DISPATCH(p, smem_yz_t<double>(p->g), smem_yz_t<float>(p->g));
+}
+int mm_yz_thread_bound(const mm_problem *p) { return DISPATCH(p, YZBound<double>::v, YZBound<float>::v); }
+
+int mm_heff_configure(mm_problem *p, size_t sx_max)
+{
+    const size_t syz = mm_smem_yz_for(p);
+    cudaError_t e = DISPATCH(p, configure_t<double>(sx_max, syz, p->g.Pz), configure_t<float>(sx_max, syz, p->g.Pz));
     if (e) { mm_set_cuda_error(e, "cudaFuncSetAttribute"); return MM_ERR_CUDA; }
+    return MM_OK;
+}
+
+int mm_autotune(mm_problem *p, const int *tys, int nty, const int *rbs, int nrb, cudaStream_t s)
+{
+    cudaError_t e = DISPATCH(p, autotune_t<double>(p, tys, nty, rbs, nrb, s),
+                             autotune_t<float>(p, tys, nty, rbs, nrb, s));
+    if (e) { mm_set_cuda_error(e, "autotune"); return MM_ERR_CUDA; }
     return MM_OK;
 }
 
@@ -674,12 +872,12 @@ int mm_launch_min_body(mm_problem *p, cudaGraphConditionalHandle h, cudaStream_t
 
 int mm_kernel_stage_times(mm_problem *p, int reps, double *ms, const char **names, int *count, cudaStream_t s)
 {
-    static const char *nm[4] = {"xfwd_step", "yz_conv", "xinv_local", "reduce_bb"};
-    if (*count < 4) return MM_ERR_ARG;
+    static const char *nm[3] = {"xfwd_step", "yz_conv", "xinv_local_bb"};
+    if (*count < 3) return MM_ERR_ARG;
     cudaError_t e = DISPATCH(p, stage_times_t<double>(p, reps, ms, s), stage_times_t<float>(p, reps, ms, s));
     if (e) { mm_set_cuda_error(e, "stage timing"); return MM_ERR_CUDA; }
-    for (int i = 0; i < 4; ++i) names[i] = nm[i];
-    *count = 4;
+    for (int i = 0; i < 3; ++i) names[i] = nm[i];
+    *count = 3;
     return MM_OK;
 }
 

@@ -124,13 +124,13 @@ __global__ void k_fft_strided(double2 *F, int L, int logL, long stride, long inn
     double2 *S = reinterpret_cast<double2 *>(smem_raw);
     const long r = blockIdx.x;
     const long base = (r % inner) + (r / inner) * outer_stride;
-    for (int t = threadIdx.x; t < L; t += blockDim.x) S[t] = F[base + t * stride];
+    for (int t = threadIdx.x; t < L; t += blockDim.x) S[pidx(t)] = F[base + t * stride];
     __syncthreads();
     const int G = L >= 8 ? L / 8 : 1;
     const bool act = threadIdx.x < G;
     fft_row<false, false, false>(S, L, logL, act ? (int)threadIdx.x : 0, tw, 1, act);
     __syncthreads();
-    for (int t = threadIdx.x; t < L; t += blockDim.x) F[base + t * stride] = S[t];
+    for (int t = threadIdx.x; t < L; t += blockDim.x) F[base + t * stride] = S[pidx(t)];
 }
 
 template <typename T>
@@ -206,7 +206,7 @@ int mm_tensor_spectrum(mm_problem *p, const double *N_dev, cudaStream_t s)
         for (int a = 0; a < 3; ++a) {
             if (L[a] == 1) continue;
             const int thr = ((L[a] >= 8 ? L[a] / 8 : 1) + 31) & ~31;
-            const size_t sm = sizeof(double2) * L[a];
+            const size_t sm = sizeof(double2) * padded_row(L[a]);
             if (sm > 48 * 1024)
                 cudaFuncSetAttribute(k_fft_strided, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             k_fft_strided<<<(unsigned)rows[a], thr, sm, s>>>(F, L[a], ilog2(L[a]), stride[a], inner[a],
