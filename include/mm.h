@@ -233,6 +233,52 @@ MM_API int mm_hysteresis_sweep(mm_problem *prob, void *m, const double *H_list, 
                         const mm_min_opts *opts, double *mavg, mm_min_result *per_step,
                         void *stream);
 
+/*
+ * Differentiation (an extension beyond the paper, whose method only minimises).
+ *
+ * mm_energy_gradient -- G_out = scale * dU/dm with dU/dm_i = -mu0 Ms V H_eff,i
+ * (Eq. effective_field read cell-wise), the energy of mm_energy.  For
+ * automatic differentiation scale is the incoming gradient of U.  m, G_out:
+ * host or device [3][nz][ny][nx].
+ */
+MM_API int mm_energy_gradient(mm_problem *prob, const void *m, const double Hext[3], double scale, void *G_out,
+                              void *stream);
+
+/*
+ * mm_hessian_vec -- the tangent-plane second derivative at m applied to a
+ * tangent field v (units A/m; times mu0 Ms V it is the Riemannian Hessian of U):
+ *   Av = P_m((m.H) v - L v)  (= (m.H) v - P_m(L v) for tangent v),  H = H_eff(m),
+ *   L v = H_eff(v) without the external field,  P_m w = w - (m.w) m.
+ * m, v, Av: host or device [3][nz][ny][nx].  Overwrites the minimiser's work
+ * buffers (a later mm_minimize / mm_hysteresis_sweep starts from its own m).
+ */
+MM_API int mm_hessian_vec(mm_problem *prob, const void *m, const double Hext[3], const void *v, void *Av,
+                          void *stream);
+
+/*
+ * mm_adjoint_dK -- implicit adjoint at a converged minimum m of mm_minimize:
+ * the gradient of an objective J(m*(K)) with respect to the per-cell
+ * anisotropy constants.  With the operator A of mm_hessian_vec it solves
+ * A lambda = P_m(dJ/dm) by conjugate gradients (relative residual < tol, at
+ * most max_iter iterations) and returns dJdK[i] = lambda_i . P_m(dH_i/dK_i),
+ * dH_i/dK_i = (2/(mu0 Ms)) (m_i.u_i) u_i.  Example: J = <m_x> has
+ * dJ/dm = (1/N, 0, 0) in every cell.
+ * dJdm: host or device [3][nz][ny][nx] (problem precision); dJdK: host or
+ * device double [nz][ny][nx]; iters, resid (host, nullable): CG iterations and
+ * final relative residual.  Returns MM_OK, MM_ERR_NOT_CONVERGED (max_iter
+ * reached), MM_ERR_NONFINITE (A not positive on the search direction: m is
+ * not a minimum), MM_ERR_ARG, MM_ERR_OOM or MM_ERR_CUDA.  Synchronises `stream`.
+ */
+MM_API int mm_adjoint_dK(mm_problem *prob, const void *m, const double Hext[3], const void *dJdm, double *dJdK,
+                         double tol, long max_iter, long *iters, double *resid, void *stream);
+
+/*
+ * mm_set_anisotropy -- replace the per-cell anisotropy constants
+ * (host or device double [nz][ny][nx]) of an existing problem, e.g. for finite
+ * differences or parameter studies.  Synchronises `stream`.
+ */
+MM_API int mm_set_anisotropy(mm_problem *prob, const double *K_cell, void *stream);
+
 /* Sizes of a problem, for reporting and for callers that size buffers. */
 typedef struct {
     int nx, ny, nz;

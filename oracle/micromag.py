@@ -431,3 +431,58 @@ def loop_metrics(H_list, mavg):
             M_r = mavg[n, 0]
             break
     return {"H_sw": H_sw, "H_c": H_c, "M_r": M_r}
+
+
+# ----------------------------------------------------------------------------
+# Implicit adjoint at a converged minimum (differentiation extension; not in
+# the paper).  At a minimum the torque vanishes, P_m H(m; K) = 0 with
+# P_m w = w - (m.w) m.  Linearising gives A dm = P_m(dH/dK) dK with the
+# tangent-plane operator A v = (m.H) v - P_m(L v), L v = H_eff(v) without the
+# external field (all other terms are linear in m).  For an objective J(m),
+# dJ/dK_i = lambda . P_m(dH/dK_i) with A lambda = P_m(dJ/dm).
+# ----------------------------------------------------------------------------
+
+def project(m, w):
+    """Tangent-plane projection w - (m.w) m, per cell."""
+    return w - np.sum(m * w, axis=0)[None] * m
+
+
+def hessian_vec(prob: Problem, m, H, v, demag: Demag):
+    """A v = P_m((m.H) v - L v), i.e. (m.H) v - P_m(L v) for a tangent field v;
+    H = H_eff(m).  Projecting the whole product keeps iterates tangent: a
+    normal component left by rounding would otherwise be multiplied by m.H
+    (large and negative near the film's ends) at every product."""
+    Lv = heff(prob, v, (0.0, 0.0, 0.0), demag)
+    return project(m, np.sum(m * H, axis=0)[None] * v - Lv)
+
+
+def adjoint_solve(prob: Problem, m, Hext, rhs, demag: Demag, tol=1e-12, max_iter=10000):
+    """Conjugate gradients for A lam = P_m(rhs) on tangent fields."""
+    H = heff(prob, m, Hext, demag)
+    b = project(m, rhs)
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = float(np.sum(r * r))
+    bb = rr
+    it = 0
+    while rr > tol * tol * bb and it < max_iter:
+        Ap = hessian_vec(prob, m, H, p, demag)
+        alpha = rr / float(np.sum(p * Ap))
+        x += alpha * p
+        r -= alpha * Ap
+        rr_new = float(np.sum(r * r))
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        it += 1
+    return x, it
+
+
+def dJ_dK(prob: Problem, m, Hext, dJdm, demag: Demag, tol=1e-12):
+    """Gradient of an objective J(m*(K)) with respect to the per-cell K at a
+    converged minimum m*: lam . P_m(dH/dK_i), dH_i/dK_i = (2/(mu0 Ms)) (m_i.u_i) u_i."""
+    lam, it = adjoint_solve(prob, m, Hext, dJdm, demag, tol=tol)
+    u = prob.u_cells()
+    mu = np.sum(m * u, axis=0)
+    dH = (2.0 / (MU0 * prob.Ms)) * mu[None] * u
+    return np.sum(lam * project(m, dH), axis=0), it

@@ -21,9 +21,6 @@ struct NvtxRange {
 };
 }
 
-// implemented in heff.cu
-int mm_launch_field(mm_problem *p, const void *m, void *H, const double *hext, int mode, cudaStream_t s);
-int mm_launch_convert(mm_problem *p, void *dst, const double *src, long n, cudaStream_t s);
 
 static thread_local char g_cuda_err[256] = "";
 
@@ -71,14 +68,19 @@ bool grid_ok(const mm_grid *g)
            (long)g->nx * g->ny * g->nz <= (1L << 31) / 3;
 }
 
+} // namespace
+
 // Is ptr device-accessible memory (device or managed)?  Host memory
 // (pageable or pinned) is staged.
-bool is_device_ptr(const void *ptr)
+bool mm_is_device_ptr(const void *ptr)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) { cudaGetLastError(); return false; }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
+
+namespace {
+#define is_device_ptr mm_is_device_ptr
 
 int dalloc(mm_problem *p, void **ptr, size_t bytes)
 {
@@ -96,7 +98,7 @@ void free_problem(mm_problem *p)
     if (p->graph) cudaGraphDestroy(p->graph);
     void *bufs[] = {p->mbuf[0], p->mbuf[1], p->gbuf[0], p->gbuf[1], p->W, p->Nhat, p->tw_px, p->tw_py,
                     p->tw_pz, p->Kc, p->uc, p->partials, p->st, p->Hext_dev, p->stage_in, p->stage_out,
-                    p->rec_dev, p->counter};
+                    p->rec_dev, p->counter, p->adj[0], p->adj[1]};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (p->st_host) cudaFreeHost(p->st_host);
@@ -187,14 +189,30 @@ int build_graph(mm_problem *p)
     return rc;
 }
 
-// Copy `n` elements between a caller buffer and a device buffer; h2d selects direction.
-int copy_user(void *dst, const void *src, size_t bytes, bool dst_dev, bool src_dev, cudaStream_t s)
+} // namespace
+
+// Drop and recapture the minimiser graph (after a kernel parameter such as
+// the per-cell anisotropy pointer changed).
+int mm_rebuild_graph(mm_problem *p)
+{
+    if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
+    if (p->graph) { cudaGraphDestroy(p->graph); p->graph = nullptr; }
+    p->graph_ready = 0;
+    return build_graph(p);
+}
+
+// Copy bytes between a caller buffer and a device buffer (either may be host memory).
+int mm_copy_user(void *dst, const void *src, size_t bytes, bool dst_dev, bool src_dev, cudaStream_t s)
 {
     cudaMemcpyKind k = dst_dev ? (src_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice)
                                : (src_dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost);
-    CK(cudaMemcpyAsync(dst, src, bytes, k, s), "cudaMemcpyAsync");
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, k, s);
+    if (e) { mm_set_cuda_error(e, "cudaMemcpyAsync"); return MM_ERR_CUDA; }
     return MM_OK;
 }
+
+namespace {
+#define copy_user mm_copy_user
 
 bool opts_ok(const mm_min_opts *o)
 {

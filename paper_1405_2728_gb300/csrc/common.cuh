@@ -119,6 +119,7 @@ struct FieldPtrs {
     double *partials;      // [nblocks][RED_NSLOT]
     MinState *st;          // minimiser state (MODE_MIN and updates)
     unsigned *counter;     // CTAs of the current x-inverse launch that have finished (reset by the last)
+    double hscale;         // MODE_HEFF writes hscale * H (1 for the field itself)
 };
 
 // ---------------------------------------------------------------------------
@@ -140,6 +141,7 @@ struct mm_problem {
     unsigned *counter;     // completion counter of the x-inverse kernel
     int nblk_x;            // CTAs of the x kernels (= partial slots)
     int tys[8], nty;       // admissible rows-per-tile of the x kernels
+    void *adj[2];          // two more field buffers for the adjoint solver (allocated on first use)
     int rbs[16], nrb;      // admissible rows-per-batch of the y-z kernel
     MinState *st;
     MinState *st_host;     // pinned mirror
@@ -168,9 +170,16 @@ int mm_yz_thread_bound(const mm_problem *p);
 int mm_heff_configure(mm_problem *p, size_t sx_max);
 int mm_autotune(mm_problem *p, const int *tys, int nty, const int *rbs, int nrb, cudaStream_t s);
 int mm_launch_twiddles(mm_problem *p, cudaStream_t s);
+int mm_launch_field(mm_problem *p, const void *m, void *H, const double *hext, int mode, cudaStream_t s,
+                    double hscale = 1.0);
+int mm_launch_convert(mm_problem *p, void *dst, const double *src, long n, cudaStream_t s);
+int mm_rebuild_graph(mm_problem *p);
 // implemented in newell.cu
 int mm_newell_device(const mm_grid *g, double *N_dev, cudaStream_t s);
 int mm_tensor_spectrum(mm_problem *p, const double *N_dev, cudaStream_t s);
 
+// helpers (api.cu)
+bool mm_is_device_ptr(const void *ptr);
+int mm_copy_user(void *dst, const void *src, size_t bytes, bool dst_dev, bool src_dev, cudaStream_t s);
 // error bookkeeping (api.cu)
 void mm_set_cuda_error(cudaError_t e, const char *where);

@@ -458,6 +458,7 @@ __global__ void __launch_bounds__(768) k_xinv(Geom g, FieldPtrs<T> P, double hx0
     const T cx = (T)g.cex_x, cy = (T)g.cex_y, cz = (T)g.cex_z, can = (T)g.can;
     const T kfac = (T)(0.5 * g.can);  // 1/(mu0 Ms)
     const T Kuni = (T)g.K, ux = (T)g.u[0], uy = (T)g.u[1], uz = (T)g.u[2];  // converted once, not per cell
+    const T hs = (T)P.hscale;
     Acc<T> red[NSL];
 #pragma unroll
     for (int s = 0; s < NSL; ++s) red[s].zero();
@@ -490,7 +491,7 @@ __global__ void __launch_bounds__(768) k_xinv(Geom g, FieldPtrs<T> P, double hx0
         const T H1 = d1 + e1 + ka * u1 + he1;
         const T H2 = d2 + e2 + ka * u2 + he2;
         if (MODE == MODE_HEFF) {
-            P.H_out[n] = H0; P.H_out[N + n] = H1; P.H_out[2 * N + n] = H2;
+            P.H_out[n] = hs * H0; P.H_out[N + n] = hs * H1; P.H_out[2 * N + n] = hs * H2;
             continue;
         }
         red[SL_MX].add(m0); red[SL_MY].add(m1); red[SL_MZ].add(m2);
@@ -630,6 +631,7 @@ template <typename T> FieldPtrs<T> make_ptrs(mm_problem *p)
     P.tw_px = (const V *)p->tw_px; P.tw_py = (const V *)p->tw_py; P.tw_pz = (const V *)p->tw_pz;
     P.Kc = (const T *)p->Kc; P.uc = (const T *)p->uc;
     P.partials = p->partials; P.st = p->st; P.counter = p->counter;
+    P.hscale = 1.0;
     return P;
 }
 
@@ -751,12 +753,14 @@ template <typename T> cudaError_t autotune_t(mm_problem *p, const int *tys, int 
 
 // Field chain for MODE_HEFF / MODE_ENERGY on caller-provided m (and H).
 template <typename T>
-cudaError_t heff_chain_t(mm_problem *p, const void *m, void *H, const double *hext, int mode, cudaStream_t s)
+cudaError_t heff_chain_t(mm_problem *p, const void *m, void *H, const double *hext, int mode, cudaStream_t s,
+                         double hscale)
 {
     const Geom &g = p->g;
     FieldPtrs<T> P = make_ptrs<T>(p);
     P.m_src = (const T *)m;
     P.H_out = (T *)H;
+    P.hscale = hscale;
     const dim3 gx((g.ny + g.TY - 1) / g.TY, g.nz);
     const size_t sx = smem_x_t<T>(g);
     k_xfwd<T, false><<<gx, threads_x<T>(g), sx, s>>>(g, P);
@@ -855,10 +859,11 @@ int mm_autotune(mm_problem *p, const int *tys, int nty, const int *rbs, int nrb,
     return MM_OK;
 }
 
-int mm_launch_field(mm_problem *p, const void *m, void *H, const double *hext, int mode, cudaStream_t s)
+int mm_launch_field(mm_problem *p, const void *m, void *H, const double *hext, int mode, cudaStream_t s,
+                    double hscale)
 {
-    cudaError_t e = DISPATCH(p, heff_chain_t<double>(p, m, H, hext, mode, s),
-                             heff_chain_t<float>(p, m, H, hext, mode, s));
+    cudaError_t e = DISPATCH(p, heff_chain_t<double>(p, m, H, hext, mode, s, hscale),
+                             heff_chain_t<float>(p, m, H, hext, mode, s, hscale));
     if (e) { mm_set_cuda_error(e, "field kernels"); return MM_ERR_CUDA; }
     return MM_OK;
 }

@@ -86,11 +86,17 @@ def lib():
                                           POINTER(mm_min_result), c_void_p]
         L.mm_problem_info.argtypes = [c_void_p, POINTER(mm_info)]
         L.mm_kernel_times.argtypes = [c_void_p, c_void_p, dp, c_int, dp, POINTER(c_char_p), POINTER(c_int), c_void_p]
+        L.mm_energy_gradient.argtypes = [c_void_p, c_void_p, dp, c_double, c_void_p, c_void_p]
+        L.mm_hessian_vec.argtypes = [c_void_p, c_void_p, dp, c_void_p, c_void_p, c_void_p]
+        L.mm_adjoint_dK.argtypes = [c_void_p, c_void_p, dp, c_void_p, c_void_p, c_double, c_long,
+                                    POINTER(c_long), POINTER(c_double), c_void_p]
+        L.mm_set_anisotropy.argtypes = [c_void_p, c_void_p, c_void_p]
         L.mm_status_string.argtypes = [c_int]
         L.mm_status_string.restype = c_char_p
         L.mm_last_cuda_error.restype = c_char_p
         for name in ("mm_newell", "mm_newell_static", "mm_setup_geometry", "mm_destroy", "mm_heff", "mm_energy", "mm_minimize",
-                     "mm_hysteresis_sweep", "mm_problem_info", "mm_kernel_times"):
+                     "mm_hysteresis_sweep", "mm_problem_info", "mm_kernel_times", "mm_energy_gradient",
+                     "mm_hessian_vec", "mm_adjoint_dK", "mm_set_anisotropy"):
             getattr(L, name).restype = c_int
         _lib = L
     return _lib
@@ -284,3 +290,41 @@ def mm_kernel_times(prob: Problem, m, Hext, reps=20, stream=None) -> dict:
     _check(lib().mm_kernel_times(prob.handle, _ptr(m, prob.dtype, prob.shape, "m"), h[1], int(reps), ms, names,
                                  ctypes.byref(cnt), _stream(stream, m)), "mm_kernel_times")
     return {names[i].decode(): ms[i] for i in range(cnt.value)}
+
+
+def mm_energy_gradient(prob: Problem, m, Hext, G_out, scale=1.0, stream=None):
+    """G_out = scale * dU/dm = -scale * mu0 Ms V H_eff(m)."""
+    h = _vec3(Hext)
+    _check(lib().mm_energy_gradient(prob.handle, _ptr(m, prob.dtype, prob.shape, "m"), h[1], float(scale),
+                                    _ptr(G_out, prob.dtype, prob.shape, "G_out"), _stream(stream, m, G_out)),
+           "mm_energy_gradient")
+    return G_out
+
+
+def mm_hessian_vec(prob: Problem, m, Hext, v, Av, stream=None):
+    """Av = (m.H) v - P_m(L v) for a tangent field v."""
+    h = _vec3(Hext)
+    _check(lib().mm_hessian_vec(prob.handle, _ptr(m, prob.dtype, prob.shape, "m"), h[1],
+                                _ptr(v, prob.dtype, prob.shape, "v"), _ptr(Av, prob.dtype, prob.shape, "Av"),
+                                _stream(stream, m, v, Av)), "mm_hessian_vec")
+    return Av
+
+
+def mm_adjoint_dK(prob: Problem, m, Hext, dJdm, dJdK, tol=1e-10, max_iter=10000, stream=None):
+    """dJ/dK per cell at a converged minimum; returns (status, iterations, relative residual)."""
+    h = _vec3(Hext)
+    it = c_long(0)
+    res = c_double(0.0)
+    st = lib().mm_adjoint_dK(prob.handle, _ptr(m, prob.dtype, prob.shape, "m"), h[1],
+                             _ptr(dJdm, prob.dtype, prob.shape, "dJdm"),
+                             _ptr(dJdK, np.float64, prob.shape[1:], "dJdK"), float(tol), int(max_iter),
+                             ctypes.byref(it), ctypes.byref(res), _stream(stream, m, dJdm, dJdK))
+    if st not in _SOFT:
+        raise MMError(st, "mm_adjoint_dK")
+    return st, it.value, res.value
+
+
+def mm_set_anisotropy(prob: Problem, K_cell, stream=None):
+    """Replace the per-cell K (float64 (nz, ny, nx), host or device)."""
+    _check(lib().mm_set_anisotropy(prob.handle, _ptr(K_cell, np.float64, prob.shape[1:], "K_cell"),
+                                   _stream(stream, K_cell)), "mm_set_anisotropy")
