@@ -279,6 +279,29 @@ MM_API int mm_adjoint_dK(mm_problem *prob, const void *m, const double Hext[3], 
  */
 MM_API int mm_set_anisotropy(mm_problem *prob, const double *K_cell, void *stream);
 
+/*
+ * Batched sweeps (an extension; the paper sweeps one sample).  A batch
+ * references existing problems (of any sizes and precisions; the caller keeps
+ * owning them and must not destroy them while the batch exists) and runs
+ * their hysteresis sweeps together.  Each problem keeps its own device-side
+ * minimiser loop (its CUDA graph, with the launch shapes its setup autotuner
+ * chose) and gets a stream of its own; for every field value the batch issues
+ * every problem's minimisation on its stream, so the problems run
+ * concurrently on the GPU.
+ *
+ * mm_batch_sweep: as mm_hysteresis_sweep for every problem i with the same
+ * field list H_list[n][3] (host, A/m): m_list[i] (host or device, in/out) is
+ * problem i's magnetisation; mavg (host) [nprob][n][3]; per_step (host,
+ * nullable) [nprob][n].  Work is ordered after earlier work on `stream`, and
+ * `stream` is synchronised before returning.  Returns MM_OK if every
+ * minimisation converged, else the first non-OK status.
+ */
+typedef struct mm_batch mm_batch;
+MM_API int mm_batch_create(mm_problem *const *probs, int nprob, mm_batch **out);
+MM_API int mm_batch_destroy(mm_batch *batch);
+MM_API int mm_batch_sweep(mm_batch *batch, void *const *m_list, const double *H_list, int n, int start,
+                          const mm_min_opts *opts, double *mavg, mm_min_result *per_step, void *stream);
+
 /* Sizes of a problem, for reporting and for callers that size buffers. */
 typedef struct {
     int nx, ny, nz;

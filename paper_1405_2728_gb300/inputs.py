@@ -139,6 +139,25 @@ def film_128x64x2_random_K() -> Workload:
     return w
 
 
+def batch_films(count: int = 64, seed: int = 1405, max_mT: float = 50.0, step_mT: float = 2.0):
+    """``count`` films of uneven size on 3.90625 nm cubic cells: nx uniform in
+    64..512, aspect a uniform in [1, 4], ny = clamp(round(nx / a), 32, 256),
+    nz uniform in 1..4, K uniform in [0, 2000] J/m^3 (the 32x16x1 material
+    otherwise), each with its own +-max_mT sweep in step_mT steps."""
+    u = uniform(seed, 4 * count).reshape(count, 4)
+    films = []
+    for i in range(count):
+        nx = 64 + int(u[i, 0] * 449)
+        a = 1.0 + 3.0 * u[i, 1]
+        ny = int(min(256, max(32, round(nx / a))))
+        nz = 1 + int(u[i, 2] * 4)
+        h = 3.90625e-9
+        w = Workload(f"film{i}_{nx}x{ny}x{nz}", nx, ny, nz, h, h, h, K=2000.0 * float(u[i, 3]),
+                     seed=seed + i, max_mT=max_mT, step_mT=step_mT)
+        films.append(w)
+    return films
+
+
 WORKLOADS = {
     "film_32x16x1": film_32x16x1,
     "film_512x256x4": film_512x256x4,

@@ -91,12 +91,17 @@ def lib():
         L.mm_adjoint_dK.argtypes = [c_void_p, c_void_p, dp, c_void_p, c_void_p, c_double, c_long,
                                     POINTER(c_long), POINTER(c_double), c_void_p]
         L.mm_set_anisotropy.argtypes = [c_void_p, c_void_p, c_void_p]
+        L.mm_batch_create.argtypes = [POINTER(c_void_p), c_int, POINTER(c_void_p)]
+        L.mm_batch_destroy.argtypes = [c_void_p]
+        L.mm_batch_sweep.argtypes = [c_void_p, POINTER(c_void_p), dp, c_int, c_int, POINTER(mm_min_opts), dp,
+                                     POINTER(mm_min_result), c_void_p]
         L.mm_status_string.argtypes = [c_int]
         L.mm_status_string.restype = c_char_p
         L.mm_last_cuda_error.restype = c_char_p
         for name in ("mm_newell", "mm_newell_static", "mm_setup_geometry", "mm_destroy", "mm_heff", "mm_energy", "mm_minimize",
                      "mm_hysteresis_sweep", "mm_problem_info", "mm_kernel_times", "mm_energy_gradient",
-                     "mm_hessian_vec", "mm_adjoint_dK", "mm_set_anisotropy"):
+                     "mm_hessian_vec", "mm_adjoint_dK", "mm_set_anisotropy", "mm_batch_create",
+                     "mm_batch_destroy", "mm_batch_sweep"):
             getattr(L, name).restype = c_int
         _lib = L
     return _lib
@@ -328,3 +333,51 @@ def mm_set_anisotropy(prob: Problem, K_cell, stream=None):
     """Replace the per-cell K (float64 (nz, ny, nx), host or device)."""
     _check(lib().mm_set_anisotropy(prob.handle, _ptr(K_cell, np.float64, prob.shape[1:], "K_cell"),
                                    _stream(stream, K_cell)), "mm_set_anisotropy")
+
+
+class Batch:
+    """Owner of an mm_batch*; keeps its problems alive."""
+
+    def __init__(self, handle, probs):
+        self.handle = handle
+        self.probs = list(probs)
+
+    def close(self):
+        if self.handle:
+            lib().mm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mm_batch_create(probs) -> Batch:
+    arr = (c_void_p * len(probs))(*[p.handle for p in probs])
+    h = c_void_p()
+    _check(lib().mm_batch_create(arr, len(probs), ctypes.byref(h)), "mm_batch_create")
+    return Batch(h, probs)
+
+
+def mm_batch_destroy(batch: Batch):
+    batch.close()
+
+
+def mm_batch_sweep(batch: Batch, m_list, H_list, start=0, opts: mm_min_opts | None = None, stream=None):
+    """Sweep every problem of the batch over H_list (n, 3); returns
+    (status, mavg (nprob, n, 3), per_step results [nprob][n])."""
+    opts = opts or make_opts()
+    H = np.ascontiguousarray(np.asarray(H_list, dtype=np.float64).reshape(-1, 3))
+    n = H.shape[0]
+    P = len(batch.probs)
+    ptrs = (c_void_p * P)(*[_ptr(m, p.dtype, p.shape, "m") for m, p in zip(m_list, batch.probs)])
+    mavg = np.full((P, n, 3), np.nan)
+    res = (mm_min_result * (P * n))()
+    st = lib().mm_batch_sweep(batch.handle, ptrs, H.ctypes.data_as(POINTER(c_double)), n, int(start),
+                              ctypes.byref(opts), mavg.ctypes.data_as(POINTER(c_double)), res,
+                              _stream(stream, *m_list))
+    if st not in _SOFT:
+        raise MMError(st, "mm_batch_sweep")
+    return st, mavg, [list(res[i * n:(i + 1) * n]) for i in range(P)]
