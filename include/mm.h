@@ -136,11 +136,15 @@ MM_API int mm_newell_static(const mm_grid *grid, double *N_dev, void *stream);
  * captures the minimiser's CUDA graph.  precision = MM_FP64 or MM_FP32: element type of m/H and of the FFT
  * and stencil arithmetic; reductions (step sizes, energies, averages) are
  * always accumulated in double.
- * Supported in this build (else MM_ERR_UNSUPPORTED): nx <= 2048 (padded x
- * length <= 4096), nz <= 4 (padded z length <= 8), nz * Py <= 2048, and the
- * padded y-z plane of one x-frequency, 3 * nz * (Py + 1) complex values,
- * within 200 KiB of shared memory -- thin films such as 512 x 256 x 4 (FP64)
- * or 1024 x 512 x 4 (FP32).
+ * Two layouts of the y-z stage of the convolution.  Film layout (nz <= 4 and
+ * the padded y-z plane of one x-frequency, about 3 * nz * 9/8 * Py complex
+ * values, within 200 KiB of shared memory; e.g. 512 x 256 x 4 in FP64 or
+ * 1024 x 512 x 4 in FP32): one kernel per x-frequency.  Bulk layout (every
+ * other grid, e.g. 256^3 cubes): separate y, z and inverse-y passes through
+ * an extra spectrum buffer of C * nz * Py * 3 complex values.
+ * Supported in this build (else MM_ERR_UNSUPPORTED): every padded length
+ * <= 4096 (nx, ny, nz <= 2048) and one padded y row or z row, with its
+ * twiddles, within 200 KiB of shared memory.
  * On success *out receives the new problem.  Synchronises `stream`.
  */
 MM_API int mm_setup_geometry(const mm_grid *grid, const mm_material *mat, int precision, void *stream,
@@ -313,6 +317,7 @@ typedef struct {
     long tensor_bytes;         /* stored tensor spectra */
     int x_tile_rows;           /* launch shape picked by the setup autotuner: y rows per x-kernel CTA */
     int yz_batch_rows;         /* ... and y rows transformed together in the y-z kernel */
+    int bulk_layout;           /* 1: y-z stage in three passes (bulk grids), 0: one film kernel */
 } mm_info;
 MM_API int mm_problem_info(const mm_problem *prob, mm_info *info);
 

@@ -97,7 +97,7 @@ void free_problem(mm_problem *p)
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->graph) cudaGraphDestroy(p->graph);
     void *bufs[] = {p->mbuf[0], p->mbuf[1], p->gbuf[0], p->gbuf[1], p->W, p->Nhat, p->tw_px, p->tw_py,
-                    p->tw_pz, p->Kc, p->uc, p->partials, p->st, p->Hext_dev, p->stage_in, p->stage_out,
+                    p->tw_pz, p->W2, p->Kc, p->uc, p->partials, p->st, p->Hext_dev, p->stage_in, p->stage_out,
                     p->rec_dev, p->counter, p->adj[0], p->adj[1]};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -126,24 +126,60 @@ int plan(mm_problem *p)
     g.can = 2.0 / (MM_MU0 * p->mat.Ms);
     g.K = p->mat.K;
     g.u[0] = p->mat.u[0]; g.u[1] = p->mat.u[1]; g.u[2] = p->mat.u[2];
-    if (g.Px > 4096 || g.Pz > 8) return MM_ERR_UNSUPPORTED;
+    if (g.Px > 4096 || g.Py > 4096 || g.Pz > 4096) return MM_ERR_UNSUPPORTED;
     // padded shared-memory rows (one pad element per 8, see fft.cuh)
     g.rsx = padded_row(g.Hx);
     g.rsy = padded_row(g.Py);
-    if (g.rsx <= g.Hx || g.rsy <= g.Py) return MM_ERR_UNSUPPORTED;  // the kernels index rows with these strides
+    g.rsz = padded_row(g.Pz);
+    if (g.rsx <= g.Hx || g.rsy <= g.Py || g.rsz <= g.Pz) return MM_ERR_UNSUPPORTED;  // the kernels index rows with these strides
+    g.lpz = ilog2i(g.Pz);
+    g.Gz = g.Pz >= 8 ? g.Pz / 8 : 1;
     // admissible launch shapes; mm_autotune picks among them after setup
     const size_t smax = 200 * 1024;
-    {
-        // y rows per batch in the y-z kernel: divisors of 3 nz with RB*Gy
-        // threads within the kernel's bound
+    g.bulk = 0;
+    p->nrb = 0;
+    if (g.Pz <= 8) {
+        // film layout: y rows per batch in the y-z kernel, divisors of 3 nz
+        // with RB*Gy threads within the kernel's bound
         const int maxT = mm_yz_thread_bound(p), nrow = 3 * g.nz;
-        p->nrb = 0;
         for (int rb = nrow; rb >= 1 && p->nrb < 16; --rb)
             if (nrow % rb == 0 && rb * g.Gy <= maxT) p->rbs[p->nrb++] = rb;
-        if (!p->nrb) return MM_ERR_UNSUPPORTED;
-        g.RB = p->rbs[0];
-        if (mm_smem_yz_for(p) > smax) return MM_ERR_UNSUPPORTED;
+        if (p->nrb) {
+            g.RB = p->rbs[0];
+            if (mm_smem_yz_for(p) > smax) p->nrb = 0;
+        }
     }
+    if (!p->nrb) {
+        // bulk layout: separate y and z passes
+        g.bulk = 1;
+        g.RB = 1;
+        p->rbs[0] = 1;
+        p->nrb = 1;
+        const int maxT = mm_bulk_thread_bound(p);
+        if (g.Gy > maxT || g.Gz > maxT) return MM_ERR_UNSUPPORTED;
+        // z planes per y-pass CTA: up to 4, as many rows as one pass of threads covers
+        g.ZB = 0;
+        for (int zb = 4; zb >= 1; zb /= 2)
+            if (zb <= g.nz && 3 * zb * g.Gy <= maxT && mm_bulk_smem_y(p, zb) <= smax) { g.ZB = zb; break; }
+        if (!g.ZB) {
+            if (mm_bulk_smem_y(p, 1) > smax) return MM_ERR_UNSUPPORTED;
+            g.ZB = 1;
+        }
+        g.RBY = 3 * g.ZB;
+        if (g.RBY * g.Gy > maxT) g.RBY = maxT / g.Gy;
+        // y frequencies per z-pass CTA: runs of KB*3 complex values along y
+        // coalesce; keep two CTAs per SM (<= 113 KiB each) where possible
+        g.KB = 0;
+        for (int kb = 16; kb >= 1; kb /= 2)
+            if (kb <= g.Py && mm_bulk_smem_z(p, kb) <= 113 * 1024) { g.KB = kb; break; }
+        if (!g.KB) {
+            if (mm_bulk_smem_z(p, 1) > smax) return MM_ERR_UNSUPPORTED;
+            g.KB = 1;
+        }
+        g.RBZ = 3 * g.KB;
+        if (g.RBZ * g.Gz > maxT) g.RBZ = maxT / g.Gz;
+    }
+    g.nbody = g.bulk ? 5 : 3;
     // y rows per CTA in the x kernels: powers of two up to 16 (and up to the
     // next power of two of ny) within 768 threads and the shared-memory cap
     p->nty = 0;
@@ -288,6 +324,7 @@ extern "C" int mm_setup_geometry(const mm_grid *grid, const mm_material *mat, in
         if ((rc = dalloc(p, &p->mbuf[0], F)) || (rc = dalloc(p, &p->mbuf[1], F)) ||
             (rc = dalloc(p, &p->gbuf[0], F)) || (rc = dalloc(p, &p->gbuf[1], F)) ||
             (rc = dalloc(p, &p->W, Wb)) || (rc = dalloc(p, &p->Nhat, Tb)) ||
+            (g.bulk && (rc = dalloc(p, &p->W2, (size_t)g.C * 3 * g.nz * g.Py * vsz))) ||
             (rc = dalloc(p, &p->tw_px, g.Px * vsz)) || (rc = dalloc(p, &p->tw_py, g.Py * vsz)) ||
             (rc = dalloc(p, &p->tw_pz, g.Pz * vsz)) ||
             (rc = dalloc(p, (void **)&p->partials, sizeof(double) * RED_NSLOT * (size_t)p->nblk_x)) ||
@@ -364,6 +401,7 @@ extern "C" int mm_problem_info(const mm_problem *p, mm_info *info)
     info->tensor_bytes = (long)g.C * (g.Pz / 2 + 1) * (g.Py / 2 + 1) * 6 * (long)p->esz;
     info->x_tile_rows = g.TY;
     info->yz_batch_rows = g.RB;
+    info->bulk_layout = g.bulk;
     return MM_OK;
 }
 

@@ -90,6 +90,15 @@ struct Geom {
     int TY;                // y rows per CTA in the x kernels
     int RB;                // y rows transformed at once in the y-z kernel (divides 3 nz)
     int rsx, rsy;          // smem row strides (complex elements) of the x and y FFT rows
+    // bulk layout (grids whose padded y-z plane does not fit one CTA): the
+    // y-z stage runs as three passes, y forward / z convolution / y inverse
+    int bulk;              // 0: film layout (one y-z kernel), 1: bulk layout
+    int ZB;                // z planes per CTA of the y passes
+    int RBY;               // y rows transformed at once in the y passes
+    int KB;                // y frequencies per CTA of the z pass
+    int RBZ;               // z rows transformed at once in the z pass
+    int lpz, Gz, rsz;      // log2(Pz), threads per z row, smem stride of a z row
+    int nbody;             // kernels per minimiser iteration (3 film, 5 bulk)
     long N;                // cells
     double dx, dy, dz;
     double Ms;
@@ -110,6 +119,7 @@ struct FieldPtrs {
     T *mbuf[2];            // minimiser iterate buffers
     T *gbuf[2];            // projected-gradient buffers
     V *W;                  // spectrum [C][nz][ny][3] (x-frequency slowest, component fastest)
+    V *W2;                 // bulk layout only: y-transformed spectrum [C][nz][Py][3]
     const T *Nhat;         // tensor spectra [C][Pz/2+1][Py/2+1][6], scaled by -Ms/(Px Py Pz)
     const V *tw_px;        // exp(-2 pi i t/Px), t < Px
     const V *tw_py;        // exp(-2 pi i t/Py), t < Py
@@ -134,6 +144,7 @@ struct mm_problem {
     // device memory
     void *mbuf[2], *gbuf[2];
     void *W;
+    void *W2;              // bulk layout only
     void *Nhat;
     void *tw_px, *tw_py, *tw_pz;
     void *Kc, *uc;
@@ -174,6 +185,14 @@ int mm_launch_field(mm_problem *p, const void *m, void *H, const double *hext, i
                     double hscale = 1.0);
 int mm_launch_convert(mm_problem *p, void *dst, const double *src, long n, cudaStream_t s);
 int mm_rebuild_graph(mm_problem *p);
+// implemented in bulk.cu: the three y-z passes of the bulk layout (pass -1:
+// all three in order; 0, 1, 2: only that one)
+cudaError_t mm_bulk_conv(const Geom &g, const FieldPtrs<double> &P, cudaStream_t s, int pass);
+cudaError_t mm_bulk_conv(const Geom &g, const FieldPtrs<float> &P, cudaStream_t s, int pass);
+size_t mm_bulk_smem_y(const mm_problem *p, int zb);
+size_t mm_bulk_smem_z(const mm_problem *p, int kb);
+int mm_bulk_thread_bound(const mm_problem *p);
+cudaError_t mm_bulk_configure(const mm_problem *p);
 // implemented in newell.cu
 int mm_newell_device(const mm_grid *g, double *N_dev, cudaStream_t s);
 int mm_tensor_spectrum(mm_problem *p, const double *N_dev, cudaStream_t s);

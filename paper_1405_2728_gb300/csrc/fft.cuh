@@ -29,6 +29,12 @@ __host__ __device__ __forceinline__ int pidx(int i) { return i + (i >> 3); }
 // element so that consecutive rows start in different banks
 __host__ __device__ __forceinline__ int padded_row(int L) { return L + (L >> 3) + 1; }
 
+// copy a twiddle table of n complex values into shared memory (all threads)
+template <typename V> __device__ __forceinline__ void load_twiddles(V *dst, const V *src, int n)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
 // 2-point DFT
 template <bool HIN, typename V> __device__ __forceinline__ void dft2(V &a0, V &a1)
 {

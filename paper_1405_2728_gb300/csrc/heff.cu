@@ -62,12 +62,6 @@ template <int PZ, bool INV, typename V> __device__ __forceinline__ V tw_pz(V v, 
     return o;
 }
 
-// copy a twiddle table of n complex values into shared memory
-template <typename V> __device__ __forceinline__ void load_twiddles(V *dst, const V *src, int n)
-{
-    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
-}
-
 // ---------------------------------------------------------------------------
 // k_xfwd
 // ---------------------------------------------------------------------------
@@ -559,7 +553,7 @@ __global__ void __launch_bounds__(768) k_xinv(Geom g, FieldPtrs<T> P, double hx0
     __syncthreads();
     if (!s_last || warp != 0) return;
     __threadfence();
-    finish_iteration<MODE>(g, P.partials, gridDim.x * gridDim.y, st, h, use_cond, 3);
+    finish_iteration<MODE>(g, P.partials, gridDim.x * gridDim.y, st, h, use_cond, g.nbody);
     if (lane == 0) *P.counter = 0u;
 }
 
@@ -627,7 +621,7 @@ template <typename T> FieldPtrs<T> make_ptrs(mm_problem *p)
     P.m_src = nullptr; P.H_out = nullptr;
     P.mbuf[0] = (T *)p->mbuf[0]; P.mbuf[1] = (T *)p->mbuf[1];
     P.gbuf[0] = (T *)p->gbuf[0]; P.gbuf[1] = (T *)p->gbuf[1];
-    P.W = (V *)p->W; P.Nhat = (const T *)p->Nhat;
+    P.W = (V *)p->W; P.W2 = (V *)p->W2; P.Nhat = (const T *)p->Nhat;
     P.tw_px = (const V *)p->tw_px; P.tw_py = (const V *)p->tw_py; P.tw_pz = (const V *)p->tw_pz;
     P.Kc = (const T *)p->Kc; P.uc = (const T *)p->uc;
     P.partials = p->partials; P.st = p->st; P.counter = p->counter;
@@ -671,12 +665,19 @@ cudaError_t launch_yz_any(const Geom &g, const FieldPtrs<T> &P, cudaStream_t s)
     }
 }
 
+// the y-z stage: the film kernel, or the three passes of the bulk layout
+template <typename T>
+cudaError_t launch_conv(const Geom &g, const FieldPtrs<T> &P, cudaStream_t s)
+{
+    return g.bulk ? mm_bulk_conv(g, P, s, -1) : launch_yz_any<T>(g, P, s);
+}
+
 template <typename T, int PZ> cudaError_t set_yz_attr(size_t smem)
 {
     return cudaFuncSetAttribute(k_yz<T, PZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <typename T> cudaError_t configure_t(size_t sx, size_t syz, int Pz)
+template <typename T> cudaError_t configure_t(size_t sx, size_t syz, int Pz, int bulk)
 {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_xfwd<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx))) return e;
@@ -684,6 +685,7 @@ template <typename T> cudaError_t configure_t(size_t sx, size_t syz, int Pz)
     if ((e = cudaFuncSetAttribute(k_xinv<T, MODE_HEFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx))) return e;
     if ((e = cudaFuncSetAttribute(k_xinv<T, MODE_ENERGY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx))) return e;
     if ((e = cudaFuncSetAttribute(k_xinv<T, MODE_MIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx))) return e;
+    if (bulk) return cudaSuccess;
     switch (Pz) {
     case 1: return set_yz_attr<T, 1>(syz);
     case 2: return set_yz_attr<T, 2>(syz);
@@ -730,7 +732,7 @@ template <typename T> cudaError_t autotune_t(mm_problem *p, const int *tys, int 
     g.TY = bty;
     best = 1e30f;
     int brb = rbs[0];
-    for (int i = 0; i < nrb && !e; ++i) {
+    for (int i = 0; i < nrb && !e && !g.bulk; ++i) {
         g.RB = rbs[i];
         float tmin = 1e30f;
         for (int r = 0; r < 3 && !e; ++r) {
@@ -766,7 +768,7 @@ cudaError_t heff_chain_t(mm_problem *p, const void *m, void *H, const double *he
     k_xfwd<T, false><<<gx, threads_x<T>(g), sx, s>>>(g, P);
     cudaError_t e = cudaGetLastError();
     if (e) return e;
-    if ((e = launch_yz_any<T>(g, P, s))) return e;
+    if ((e = launch_conv<T>(g, P, s))) return e;
     if (mode == MODE_HEFF)
         k_xinv<T, MODE_HEFF><<<gx, threads_x<T>(g), sx, s>>>(g, P, hext[0], hext[1], hext[2], 0, 0);
     else
@@ -784,7 +786,7 @@ cudaError_t min_body_t(mm_problem *p, cudaGraphConditionalHandle h, cudaStream_t
     k_xfwd<T, true><<<gx, threads_x<T>(g), sx, s>>>(g, P);
     cudaError_t e = cudaGetLastError();
     if (e) return e;
-    if ((e = launch_yz_any<T>(g, P, s))) return e;
+    if ((e = launch_conv<T>(g, P, s))) return e;
     k_xinv<T, MODE_MIN><<<gx, threads_x<T>(g), sx, s>>>(g, P, 0.0, 0.0, 0.0, h, use_cond);
     return cudaGetLastError();
 }
@@ -796,29 +798,38 @@ cudaError_t stage_times_t(mm_problem *p, int reps, double *ms, cudaStream_t s)
     FieldPtrs<T> P = make_ptrs<T>(p);
     const dim3 gx((g.ny + g.TY - 1) / g.TY, g.nz);
     const size_t sx = smem_x_t<T>(g);
-    cudaEvent_t ev[4];
-    for (int i = 0; i < 4; ++i)
+    const int nst = g.bulk ? 5 : 3;
+    cudaEvent_t ev[6];
+    for (int i = 0; i <= nst; ++i)
         if (cudaEventCreate(&ev[i])) return cudaGetLastError();
-    double acc[3] = {0, 0, 0};
+    double acc[5] = {0, 0, 0, 0, 0};
     cudaError_t e = cudaSuccess;
     for (int r = 0; r < reps && !e; ++r) {
-        cudaEventRecord(ev[0], s);
+        int i = 0;
+        cudaEventRecord(ev[i++], s);
         k_xfwd<T, true><<<gx, threads_x<T>(g), sx, s>>>(g, P);
-        cudaEventRecord(ev[1], s);
-        launch_yz_any<T>(g, P, s);
-        cudaEventRecord(ev[2], s);
+        cudaEventRecord(ev[i++], s);
+        if (g.bulk) {
+            for (int pass = 0; pass < 3; ++pass) {
+                mm_bulk_conv(g, P, s, pass);
+                cudaEventRecord(ev[i++], s);
+            }
+        } else {
+            launch_yz_any<T>(g, P, s);
+            cudaEventRecord(ev[i++], s);
+        }
         k_xinv<T, MODE_MIN><<<gx, threads_x<T>(g), sx, s>>>(g, P, 0.0, 0.0, 0.0, 0, 0);
-        cudaEventRecord(ev[3], s);
+        cudaEventRecord(ev[i++], s);
         if ((e = cudaGetLastError())) break;
-        if ((e = cudaEventSynchronize(ev[3]))) break;
-        for (int i = 0; i < 3; ++i) {
+        if ((e = cudaEventSynchronize(ev[nst]))) break;
+        for (int k = 0; k < nst; ++k) {
             float t = 0;
-            cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
-            acc[i] += t;
+            cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            acc[k] += t;
         }
     }
-    for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
-    for (int i = 0; i < 3; ++i) ms[i] = acc[i] / (reps > 0 ? reps : 1);
+    for (int i = 0; i <= nst; ++i) cudaEventDestroy(ev[i]);
+    for (int i = 0; i < nst; ++i) ms[i] = acc[i] / (reps > 0 ? reps : 1);
     return e;
 }
 
@@ -845,8 +856,10 @@ int mm_yz_thread_bound(const mm_problem *p) { return DISPATCH(p, YZBound<double>
 
 int mm_heff_configure(mm_problem *p, size_t sx_max)
 {
-    const size_t syz = mm_smem_yz_for(p);
-    cudaError_t e = DISPATCH(p, configure_t<double>(sx_max, syz, p->g.Pz), configure_t<float>(sx_max, syz, p->g.Pz));
+    const size_t syz = p->g.bulk ? 0 : mm_smem_yz_for(p);
+    cudaError_t e = DISPATCH(p, configure_t<double>(sx_max, syz, p->g.Pz, p->g.bulk),
+                             configure_t<float>(sx_max, syz, p->g.Pz, p->g.bulk));
+    if (!e && p->g.bulk) e = mm_bulk_configure(p);
     if (e) { mm_set_cuda_error(e, "cudaFuncSetAttribute"); return MM_ERR_CUDA; }
     return MM_OK;
 }
@@ -877,12 +890,14 @@ int mm_launch_min_body(mm_problem *p, cudaGraphConditionalHandle h, cudaStream_t
 
 int mm_kernel_stage_times(mm_problem *p, int reps, double *ms, const char **names, int *count, cudaStream_t s)
 {
-    static const char *nm[3] = {"xfwd_step", "yz_conv", "xinv_local_bb"};
-    if (*count < 3) return MM_ERR_ARG;
+    static const char *film[3] = {"xfwd_step", "yz_conv", "xinv_local_bb"};
+    static const char *bulk[5] = {"xfwd_step", "y_fwd", "z_conv", "y_inv", "xinv_local_bb"};
+    const int nst = p->g.bulk ? 5 : 3;
+    if (*count < nst) return MM_ERR_ARG;
     cudaError_t e = DISPATCH(p, stage_times_t<double>(p, reps, ms, s), stage_times_t<float>(p, reps, ms, s));
     if (e) { mm_set_cuda_error(e, "stage timing"); return MM_ERR_CUDA; }
-    for (int i = 0; i < 3; ++i) names[i] = nm[i];
-    *count = 3;
+    for (int i = 0; i < nst; ++i) names[i] = p->g.bulk ? bulk[i] : film[i];
+    *count = nst;
     return MM_OK;
 }
 

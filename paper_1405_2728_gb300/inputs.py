@@ -105,6 +105,8 @@ class Workload:
     step_mT: float = 1.0
     tilt_deg: float = 1.0
     K_cell: np.ndarray | None = None  # per-cell K (nz, ny, nx) or None
+    u_cell: np.ndarray | None = None  # per-cell easy axes (3, nz, ny, nx) or None
+    H_list: np.ndarray | None = None  # explicit field values (n, 3) A/m, else the SP1 sweep
 
     @property
     def shape(self):
@@ -118,6 +120,8 @@ class Workload:
         return tilted_uniform_m(self.shape, self.seed)
 
     def fields(self) -> np.ndarray:
+        if self.H_list is not None:
+            return self.H_list
         return sp1_sweep(self.max_mT, self.step_mT, self.tilt_deg)
 
 
@@ -136,6 +140,46 @@ def film_128x64x2_random_K() -> Workload:
     """500 x 250 x 10 nm film on 128 x 64 x 2 cells, per-cell K uniform in [300, 700] J/m^3."""
     w = Workload("film_128x64x2_randK", 128, 64, 2, 500e-9 / 128, 250e-9 / 64, 5e-9)
     w.K_cell = uniform(w.seed, w.ncells, 300.0, 700.0).reshape(w.shape)
+    return w
+
+
+def voronoi_grains(shape, cell, count: int, seed: int) -> np.ndarray:
+    """Grain index (nz, ny, nx) of every cell: ``count`` seed points uniform in
+    the box, each cell (by its centre) to the nearest seed in Euclidean
+    distance, ties to the lower seed index."""
+    nz, ny, nx = shape
+    dx, dy, dz = cell
+    pts = uniform(seed, 3 * count).reshape(count, 3) * np.array([nx * dx, ny * dy, nz * dz])
+    xs = (np.arange(nx) + 0.5) * dx
+    ys = (np.arange(ny) + 0.5) * dy
+    grain = np.empty(shape, dtype=np.int32)
+    dxy = (xs[None, None, :] - pts[:, 0, None, None]) ** 2 + (ys[None, :, None] - pts[:, 1, None, None]) ** 2
+    for z in range(nz):
+        d = dxy + ((z + 0.5) * dz - pts[:, 2, None, None]) ** 2
+        grain[z] = np.argmin(d, axis=0)  # first minimum: ties go to the lower index
+    return grain
+
+
+def ramp_sweep(max_T: float, step_T: float, axis=(1.0, 0.0, 0.0)) -> np.ndarray:
+    """Field values (n, 3) in A/m along ``axis``: 0 -> +max_T in step_T steps,
+    then down to -max_T (481 values for 8 T / 50 mT)."""
+    n = int(round(max_T / step_T))
+    b = [step_T * i for i in range(n + 1)] + [max_T - step_T * i for i in range(1, 2 * n + 1)]
+    return np.outer(np.array(b) / MU0, np.asarray(axis, dtype=np.float64))
+
+
+def granular_cube(n: int = 256, grains: int = 64, seed: int = 1405, edge: float = 512e-9) -> Workload:
+    """Granular hard-magnet cube: ``edge`` per side on n^3 cubic cells,
+    ``grains`` Voronoi grains from seeded points, each grain with its own
+    uniaxial easy axis uniform on the sphere; K = 4.3e6 J/m^3,
+    Ms = 1.28e6 A/m, A = 7.7e-12 J/m; initial m = +x with the seeded 1e-3
+    tilt; field along x, 0 -> +8 T -> -8 T in 50 mT steps."""
+    h = edge / n
+    w = Workload(f"cube_{n}^3_{grains}grains", n, n, n, h, h, h, Ms=1.28e6, A=7.7e-12, K=4.3e6, seed=seed)
+    grain = voronoi_grains(w.shape, (h, h, h), grains, seed)
+    axes = random_unit_m((1, 1, grains), seed + 1).reshape(3, grains)
+    w.u_cell = np.ascontiguousarray(axes[:, grain])
+    w.H_list = ramp_sweep(8.0, 0.05)
     return w
 
 
@@ -162,4 +206,9 @@ WORKLOADS = {
     "film_32x16x1": film_32x16x1,
     "film_512x256x4": film_512x256x4,
     "film_128x64x2_randK": film_128x64x2_random_K,
+}
+
+# bulk workloads (a different material and field protocol)
+BULK_WORKLOADS = {
+    "cube_256": granular_cube,
 }

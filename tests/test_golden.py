@@ -43,3 +43,30 @@ def test_splitmix64_known_sequence():
     assert [hex(int(v)) for v in z] == ["0xe220a8397b1dcdaf", "0x6e789e6aa1b965f4", "0x6c45d188009454f"]
     u = inputs.uniform(1405, 1000)
     assert u.min() >= 0 and u.max() < 1 and abs(u.mean() - 0.5) < 0.05
+
+
+def test_granular_cube_inputs():
+    # small instance of the granular-cube generator: Voronoi grains by brute
+    # force, unit axes, the 0 -> +8 T -> -8 T ramp in 50 mT steps
+    w = inputs.granular_cube(10, 5, seed=7, edge=20e-9)
+    assert (w.Ms, w.A, w.K) == (1.28e6, 7.7e-12, 4.3e6)
+    assert w.u_cell.shape == (3, 10, 10, 10)
+    assert np.allclose(np.linalg.norm(w.u_cell, axis=0), 1.0, atol=1e-14)
+    pts = inputs.uniform(7, 15).reshape(5, 3) * 20e-9
+    grain = inputs.voronoi_grains((10, 10, 10), (2e-9,) * 3, 5, 7)
+    for (z, y, x) in [(0, 0, 0), (9, 9, 9), (3, 7, 1), (5, 0, 8)]:
+        c = (np.array([x, y, z]) + 0.5) * 2e-9
+        d = np.sum((pts - c) ** 2, axis=1)
+        assert grain[z, y, x] == int(np.argmin(d))
+    # each grain's cells share one axis
+    for gi in range(5):
+        sel = grain == gi
+        if sel.any():
+            ax = w.u_cell[:, sel]
+            assert np.allclose(ax, ax[:, :1])
+    H = inputs.ramp_sweep(8.0, 0.05)
+    assert H.shape == (481, 3)
+    b = H[:, 0] * inputs.MU0
+    assert abs(b[0]) < 1e-15 and abs(b[160] - 8.0) < 1e-12 and abs(b[-1] + 8.0) < 1e-12
+    assert np.all(np.diff(b[:161]) > 0) and np.all(np.diff(b[160:]) < 0)
+    assert np.all(H[:, 1:] == 0)

@@ -1,0 +1,156 @@
+"""GPU parity of the bulk layout of the convolution (separate y, z and
+inverse-y passes, used for grids whose padded y-z plane does not fit one
+CTA: nz > 4 or long y rows) against the CPU oracle, and the 256^3 granular
+cube at full size.
+
+Bars: FP64 H_eff rel-L2 <= 1e-10 (as for films); FP32 rel-L2 <= 3e-6 on
+small grids.  At 256^3 (padded 512^3), where the oracle's quad-precision
+tensor is out of reach, the full-size runs are pinned by properties that hold
+at any size -- the demagnetising factors of a uniformly magnetised cube are
+exactly 1/3 along each axis and 0 off the diagonal, so the mean demag field
+of uniform m is -Ms/3 m -- by sampled tensor entries against the quad oracle,
+and the FP32 field against the FP64 field (rel-L2 <= 1e-5: float rounding
+of a 512-point transform per axis)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import micromag as om
+from paper_1405_2728_gb300 import inputs
+from gpu_cases import dev, make_pair, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+CELL = (2e-9, 2e-9, 2e-9)
+BULK_GRIDS = [(1, 1, 5), (2, 3, 5), (7, 5, 6), (12, 10, 9), (16, 16, 16), (9, 33, 17), (24, 20, 18)]
+
+
+def _info(mm, prob):
+    return mm.mm_problem_info(prob)
+
+
+@pytest.mark.parametrize("grid", BULK_GRIDS + [(16, 1024, 2)])
+def test_bulk_heff_matches_oracle(mmlib, grid):
+    nx, ny, nz = grid
+    cell = (3.90625e-9, 3.90625e-9, 5e-9) if nz == 2 else CELL
+    prob, oprob = make_pair(mmlib, nx, ny, nz, cell, K=2e5, u=(0.0, 0.6, 0.8))
+    assert _info(mmlib, prob)["bulk_layout"] == 1
+    m = inputs.random_unit_m(oprob.shape, seed=300 + nx + 7 * ny + 31 * nz)
+    Hext = np.array([2.0e4, -5.0e3, 9.0e3])
+    H = torch.empty((3, nz, ny, nx), dtype=torch.float64, device="cuda")
+    mmlib.mm_heff(prob, dev(m), Hext, H)
+    ref = om.heff(oprob, m, Hext, om.Demag(oprob))
+    assert rel_l2(H.cpu().numpy(), ref) <= 1e-10
+
+
+@pytest.mark.parametrize("grid", [(2, 3, 5), (12, 10, 9), (24, 20, 18)])
+def test_bulk_heff_fp32(mmlib, grid):
+    nx, ny, nz = grid
+    prob, oprob = make_pair(mmlib, nx, ny, nz, CELL, precision=mmlib.MM_FP32)
+    assert _info(mmlib, prob)["bulk_layout"] == 1
+    m = inputs.random_unit_m(oprob.shape, seed=17 + nz)
+    Hext = np.array([1.0e4, 2.0e3, -3.0e3])
+    H = torch.empty((3, nz, ny, nx), dtype=torch.float32, device="cuda")
+    mmlib.mm_heff(prob, dev(m, torch.float32), Hext, H)
+    ref = om.heff(oprob, m.astype(np.float32).astype(np.float64), Hext, om.Demag(oprob))
+    assert rel_l2(H.cpu().numpy(), ref) <= 3e-6
+
+
+def small_cube(mm, n=12, grains=8, precision=0):
+    w = inputs.granular_cube(n, grains, seed=1405, edge=n * 2e-9)
+    prob, oprob = make_pair(mm, n, n, n, (w.dx, w.dy, w.dz), Ms=w.Ms, A=w.A, K=w.K, u_cell=w.u_cell,
+                            precision=precision)
+    return w, prob, oprob
+
+
+def test_granular_cube_energy_matches_oracle(mmlib):
+    w, prob, oprob = small_cube(mmlib, 16, 8)
+    m = inputs.random_unit_m(oprob.shape, 44)
+    Hext = (3e5, -1e5, 2e5)
+    E = mmlib.mm_energy(prob, dev(m), Hext)
+    ref = om.energy(oprob, m, Hext, om.Demag(oprob))
+    keys = ["demag", "exchange", "anisotropy", "zeeman", "total"]
+    scale = max(abs(ref[k]) for k in keys)
+    for i, k in enumerate(keys):
+        assert abs(E[i] - ref[k]) <= 1e-11 * scale, (k, E[i], ref[k])
+
+
+def test_granular_cube_fixed_steps_follow_the_oracle(mmlib):
+    w, prob, oprob = small_cube(mmlib, 12, 8)
+    m0 = inputs.random_unit_m(oprob.shape, 8)
+    H = w.fields()[20]  # +1 T along x
+    m = dev(m0)
+    st, r = mmlib.mm_minimize(prob, m, H, mmlib.make_opts(tol=0.0, max_iter=25))
+    assert st == mmlib.MM_ERR_NOT_CONVERGED and r.iters == 25
+    ref = om.minimize(oprob, m0, H, om.Demag(oprob), tol=0.0, max_iter=25)
+    assert rel_l2(m.cpu().numpy(), ref.m) <= 1e-8
+    assert abs(r.max_torque - ref.max_torque) <= 1e-7 * ref.max_torque
+
+
+def test_granular_cube_sweep_matches_oracle(mmlib):
+    # the cube's ramp 0 -> +8 T -> -8 T, in 1 T steps on a 12^3 cube
+    w, prob, oprob = small_cube(mmlib, 12, 8)
+    F = inputs.ramp_sweep(8.0, 1.0)
+    tol = 1e-5
+    mavg_ref, res_ref, _ = om.sweep(oprob, w.initial_m(), F, om.Demag(oprob), tol=tol)
+    m = dev(w.initial_m())
+    st, mavg, res = mmlib.mm_hysteresis_sweep(prob, m, F, opts=mmlib.make_opts(tol=tol))
+    assert st == mmlib.MM_OK and all(r.converged for r in res)
+    # From the +x start every grain relaxes to the end of its easy axis nearer
+    # +x, then rotates reversibly toward +x and back: no switching up to the
+    # return to 0 T (the first 17 field values), so both loops agree value by
+    # value there.  Under negative fields grains switch, and which one goes
+    # first is decided by rounding (R17); the loops are compared at their end.
+    assert np.max(np.abs(mavg[:17] - mavg_ref[:17])) < 1e-5
+    # the loops end saturated along -x on both sides
+    assert abs(mavg[-1, 0] - mavg_ref[-1, 0]) < 1e-3
+
+
+def test_cube_256_full_size(mmlib):
+    w = inputs.granular_cube()  # 256^3 cells, 64 grains
+    n = w.nx
+    cell = (w.dx, w.dy, w.dz)
+    grid = mmlib.make_grid(n, n, n, *cell)
+    # (1) sampled tensor entries against the quad oracle, including the farthest offsets
+    N = torch.empty((6, n, n, n), dtype=torch.float64, device="cuda")
+    mmlib.mm_newell(grid, N)
+    rng = np.random.default_rng(256)
+    offs = [(n - 1, n - 1, n - 1), (n - 1, 0, 0), (0, n - 1, 0), (0, 0, n - 1), (0, 0, 0), (1, 0, 0)]
+    offs += [tuple(int(v) for v in rng.integers(n, size=3)) for _ in range(10)]
+    for (i, j, k) in offs:
+        ref = om.newell_entry(i, j, k, *cell)
+        got = N[:, k, j, i].cpu().numpy()
+        assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref)) + 1e-22, (i, j, k, got, ref)
+    del N
+    torch.cuda.empty_cache()
+    # (2) uniform m, no exchange/anisotropy/Zeeman contribution: <H> = -Ms/3 m exactly
+    mu = np.zeros((3, n, n, n))
+    mu[0] = 0.6
+    mu[2] = 0.8
+    for precision, dt, bar in ((mmlib.MM_FP64, torch.float64, 1e-11), (mmlib.MM_FP32, torch.float32, 2e-6)):
+        prob = mmlib.mm_setup_geometry(grid, mmlib.make_material(w.Ms, w.A, 0.0), precision)
+        assert mmlib.mm_problem_info(prob)["bulk_layout"] == 1
+        H = torch.empty((3, n, n, n), dtype=dt, device="cuda")
+        mmlib.mm_heff(prob, dev(mu, dt), (0.0, 0.0, 0.0), H)
+        mean = H.double().mean(dim=(1, 2, 3)).cpu().numpy()
+        assert np.max(np.abs(mean - (-w.Ms / 3) * np.array([0.6, 0.0, 0.8]))) <= bar * w.Ms, mean
+        del prob, H
+        torch.cuda.empty_cache()
+    # (3) the granular workload: FP32 field and energy against the FP64 run
+    m0 = w.initial_m()
+    Hext = w.fields()[40]  # +2 T
+    out = {}
+    for precision, dt in ((mmlib.MM_FP64, torch.float64), (mmlib.MM_FP32, torch.float32)):
+        prob = mmlib.mm_setup_geometry(grid, mmlib.make_material(w.Ms, w.A, w.K, u_cell=w.u_cell), precision)
+        H = torch.empty((3, n, n, n), dtype=dt, device="cuda")
+        md = dev(m0, dt)
+        mmlib.mm_heff(prob, md, Hext, H)
+        E = mmlib.mm_energy(prob, md, Hext)
+        out[precision] = (H.double(), np.array(E))
+        del prob, md
+        torch.cuda.empty_cache()
+    H64, E64 = out[mmlib.MM_FP64]
+    H32, E32 = out[mmlib.MM_FP32]
+    err = float(torch.linalg.vector_norm(H32 - H64) / torch.linalg.vector_norm(H64))
+    assert err <= 1e-5, err
+    assert np.max(np.abs(E32 - E64)) <= 1e-5 * np.max(np.abs(E64)), (E32, E64)
