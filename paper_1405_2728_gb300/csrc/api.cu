@@ -126,6 +126,12 @@ int plan(mm_problem *p)
     g.can = 2.0 / (MM_MU0 * p->mat.Ms);
     g.K = p->mat.K;
     g.u[0] = p->mat.u[0]; g.u[1] = p->mat.u[1]; g.u[2] = p->mat.u[2];
+    g.fcex_x = (float)g.cex_x; g.fcex_y = (float)g.cex_y; g.fcex_z = (float)g.cex_z;
+    g.fcan = (float)g.can; g.fK = (float)g.K;
+    g.fu[0] = (float)g.u[0]; g.fu[1] = (float)g.u[1]; g.fu[2] = (float)g.u[2];
+    g.fd_nx.init(gr.nx); g.fd_ny.init(gr.ny);
+    g.fd_padx.init(g.Px - gr.nx > 0 ? g.Px - gr.nx : 1);
+    g.fd_pady.init(g.Py - gr.ny > 0 ? g.Py - gr.ny : 1);
     if (g.Px > 4096 || g.Py > 4096 || g.Pz > 4096) return MM_ERR_UNSUPPORTED;
     // padded shared-memory rows (one pad element per 8, see fft.cuh)
     g.rsx = padded_row(g.Hx);
@@ -187,6 +193,7 @@ int plan(mm_problem *p)
         if (3 * ty * g.Gx <= 768 && mm_smem_x_for(p, ty) <= smax) p->tys[p->nty++] = ty;
     if (!p->nty) return MM_ERR_UNSUPPORTED;
     g.TY = p->tys[p->nty - 1];
+    g.lty = ilog2i(g.TY);
     // partial sums are sized for the smallest tile (most CTAs)
     p->nblk_x = ((gr.ny + p->tys[0] - 1) / p->tys[0]) * gr.nz;
     return MM_OK;

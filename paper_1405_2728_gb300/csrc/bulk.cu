@@ -23,7 +23,7 @@ namespace {
 
 template <typename T> struct BulkBound { static constexpr int v = sizeof(T) == 8 ? 384 : 512; };
 
-template <typename T, bool INV>
+template <typename T, bool INV, int LY>
 __global__ void __launch_bounds__(BulkBound<T>::v) k_ypass(Geom g, FieldPtrs<T> P)
 {
     typedef typename cvec<T>::type V;
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(BulkBound<T>::v) k_ypass(Geom g, FieldPtrs<T> 
     for (int r0 = 0; r0 < 3 * ZB; r0 += RB) {
         const int r = r0 + rb;
         const bool act = rb < RB && r < 3 * ZB && (r % ZB) < zb;
-        fft_row<INV, !INV, INV>(S + (act ? r : 0) * rs, Py, g.lpy, j, tw, 1, act);
+        fft_row<INV, !INV, INV, 1, LY>(S + (act ? r : 0) * rs, Py, g.lpy, j, tw, act);
     }
     __syncthreads();
     const int lout = INV ? ny : Py;
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(BulkBound<T>::v) k_ypass(Geom g, FieldPtrs<T> 
     }
 }
 
-template <typename T>
+template <typename T, int LZ>
 __global__ void __launch_bounds__(BulkBound<T>::v) k_zconv(Geom g, FieldPtrs<T> P)
 {
     typedef typename cvec<T>::type V;
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(BulkBound<T>::v) k_zconv(Geom g, FieldPtrs<T> 
     for (int r0 = 0; r0 < 3 * KB; r0 += RB) {
         const int r = r0 + rb;
         const bool act = rb < RB && r < 3 * KB && (r % KB) < kb;
-        fft_row<false, true, false>(S + (act ? r : 0) * rs, Pz, g.lpz, j, tw, 1, act);
+        fft_row<false, true, false, 1, LZ>(S + (act ? r : 0) * rs, Pz, g.lpz, j, tw, act);
     }
     __syncthreads();
     // tensor product per (ky, kz); octant storage [kx][kzr][kyr][6] with the
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(BulkBound<T>::v) k_zconv(Geom g, FieldPtrs<T> 
     for (int r0 = 0; r0 < 3 * KB; r0 += RB) {
         const int r = r0 + rb;
         const bool act = rb < RB && r < 3 * KB && (r % KB) < kb;
-        fft_row<true, false, true>(S + (act ? r : 0) * rs, Pz, g.lpz, j, tw, 1, act);
+        fft_row<true, false, true, 1, LZ>(S + (act ? r : 0) * rs, Pz, g.lpz, j, tw, act);
     }
     __syncthreads();
     for (int e = tid; e < nz * kb * 3; e += nth) {
@@ -148,24 +148,59 @@ template <typename T> size_t smem_z_t(const Geom &g, int kb)
     return ((size_t)3 * kb * g.rsz + g.Pz) * sizeof(V);
 }
 
+inline int lc_of(int logL) { return MM_FFT_SPECIALISED(logL) ? logL : 0; }
+#define MM_LC_CASES(X) X(0) X(6) X(7) X(8) X(9) X(10)
+
 template <typename T> cudaError_t bulk_conv_t(const Geom &g, const FieldPtrs<T> &P, cudaStream_t s, int pass)
 {
     const dim3 gy(g.C, (g.nz + g.ZB - 1) / g.ZB), gz(g.C, (g.Py + g.KB - 1) / g.KB);
     const int ty = round32(g.RBY * g.Gy), tz = round32(g.RBZ * g.Gz);
     const size_t sy = smem_y_t<T>(g, g.ZB), sz = smem_z_t<T>(g, g.KB);
-    if (pass < 0 || pass == 0) k_ypass<T, false><<<gy, ty, sy, s>>>(g, P);
-    if (pass < 0 || pass == 1) k_zconv<T><<<gz, tz, sz, s>>>(g, P);
-    if (pass < 0 || pass == 2) k_ypass<T, true><<<gy, ty, sy, s>>>(g, P);
+    const int ly = lc_of(g.lpy), lz = lc_of(g.lpz);
+    if (pass < 0 || pass == 0) {
+        switch (ly) {
+#define C(L) case L: k_ypass<T, false, L><<<gy, ty, sy, s>>>(g, P); break;
+            MM_LC_CASES(C)
+#undef C
+        }
+    }
+    if (pass < 0 || pass == 1) {
+        switch (lz) {
+#define C(L) case L: k_zconv<T, L><<<gz, tz, sz, s>>>(g, P); break;
+            MM_LC_CASES(C)
+#undef C
+        }
+    }
+    if (pass < 0 || pass == 2) {
+        switch (ly) {
+#define C(L) case L: k_ypass<T, true, L><<<gy, ty, sy, s>>>(g, P); break;
+            MM_LC_CASES(C)
+#undef C
+        }
+    }
     return cudaGetLastError();
+}
+
+template <typename F> cudaError_t smem_attr(F *f, size_t bytes)
+{
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <typename T> cudaError_t configure_t(const Geom &g)
 {
-    cudaError_t e;
-    const int sy = (int)smem_y_t<T>(g, g.ZB), sz = (int)smem_z_t<T>(g, g.KB);
-    if ((e = cudaFuncSetAttribute(k_ypass<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy))) return e;
-    if ((e = cudaFuncSetAttribute(k_ypass<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy))) return e;
-    return cudaFuncSetAttribute(k_zconv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz);
+    cudaError_t e = cudaSuccess;
+    const size_t sy = smem_y_t<T>(g, g.ZB), sz = smem_z_t<T>(g, g.KB);
+    switch (lc_of(g.lpy)) {
+#define C(L) case L: if ((e = smem_attr(k_ypass<T, false, L>, sy)) || (e = smem_attr(k_ypass<T, true, L>, sy))) return e; break;
+        MM_LC_CASES(C)
+#undef C
+    }
+    switch (lc_of(g.lpz)) {
+#define C(L) case L: return smem_attr(k_zconv<T, L>, sz);
+        MM_LC_CASES(C)
+#undef C
+    }
+    return cudaErrorInvalidValue;
 }
 
 } // namespace

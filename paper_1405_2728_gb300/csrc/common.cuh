@@ -68,6 +68,8 @@ struct MinState {
     double energy[5];         // demag, exchange, anisotropy, zeeman, total (J) at iterate k
     double mavg[3];
     long launches;            // kernels launched by the loop body so far
+    float Hextf[3];           // Hext and tau rounded once for the float kernels
+    float tauf;
 };
 
 // Per-step record of a sweep
@@ -76,6 +78,34 @@ struct StepRecord {
     double max_torque, energy;
     long iters, evals, launches;
     int status;
+};
+
+// ---------------------------------------------------------------------------
+// Division by a runtime divisor d >= 1 through a precomputed multiplier
+// (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994, round-up variant): for 0 <= n < 2^31,
+// n / d = (umulhi(n, mul) + n) >> shift with shift = ceil(log2 d) and
+// mul = floor(2^32 (2^shift - d) / d) + 1.
+// ---------------------------------------------------------------------------
+struct FastDiv {
+    unsigned mul;
+    int shift;
+    int d;
+    __host__ __device__ void init(int dv)
+    {
+        d = dv;
+        int l = 0;
+        while ((1u << l) < (unsigned)dv) ++l;
+        shift = l;
+        mul = (unsigned)((((unsigned long long)1 << 32) * (((unsigned long long)1 << l) - (unsigned long long)dv)) /
+                         (unsigned long long)dv + 1ull);
+    }
+#ifdef __CUDACC__
+    __device__ __forceinline__ int div(int n) const
+    {
+        return (int)((__umulhi((unsigned)n, mul) + (unsigned)n) >> shift);
+    }
+#endif
 };
 
 // ---------------------------------------------------------------------------
@@ -106,7 +136,28 @@ struct Geom {
     double can;                    // 2/(mu0 Ms) (times K per cell)
     double K;                      // uniform K
     double u[3];                   // uniform axis
+    // the same constants rounded once to float for the float kernels (a
+    // conversion per thread would run on the slow FP64 pipe)
+    float fcex_x, fcex_y, fcex_z, fcan, fK, fu[3];
+    int lty;                       // log2(TY)
+    FastDiv fd_nx, fd_ny, fd_padx, fd_pady;  // divisors nx, ny, Px - nx, Py - ny
 };
+
+__host__ __device__ __forceinline__ int mm_ilog2(int v)
+{
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+// value of a double constant in the kernel's precision (float copy for float)
+template <typename T> __host__ __device__ __forceinline__ T pick(double d, float f)
+{
+    if constexpr (sizeof(T) == 4) return f;
+    else return d;
+}
+
+
 
 // Field evaluation modes of the x-inverse/local kernel
 enum { MODE_HEFF = 0, MODE_ENERGY = 1, MODE_MIN = 2 };

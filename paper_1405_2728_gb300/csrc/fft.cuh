@@ -104,6 +104,13 @@ template <int R, bool INV, bool HIN, typename V> __device__ __forceinline__ void
 // radices of the previous passes).  Thread j handles butterflies j + q G,
 // q < 8/R.  Caller guarantees visibility of the row before the call; the
 // pass ends with a barrier.
+//
+// Padded offsets in closed form (Ns, R, LR = L/R powers of two): butterfly b
+// reads elements b + r LR, whose padded offsets are pidx(b) + r (LR + LR/8)
+// when 8 divides LR; it writes elements (b - k) R + k + r Ns, k = b mod Ns,
+// whose padded offsets are 9 (b - k) + k + k/8 + r Ns + (r Ns)/8 for R = 8
+// (and likewise with (b - k) R for R < 8), since k < Ns and Ns divides or is
+// a multiple of 8.
 template <int R, bool INV, bool HIN, bool HOUT, typename V>
 __device__ __forceinline__ void stockham_pass(V *row, int L, int Ns, int j, int G,
                                               const V *__restrict__ tw, int ts, bool active)
@@ -111,19 +118,24 @@ __device__ __forceinline__ void stockham_pass(V *row, int L, int Ns, int j, int 
     constexpr int NB = 8 / R;
     V v[8];
     const int LR = L / R;
+    const int ld9 = LR + (LR >> 3);       // padded stride between the inputs of a butterfly (8 | LR)
+    const int tstep0 = (L / (Ns * R)) * ts;
     if (active) {
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
             const int b = j + q * G;
+            const int p0 = pidx(b);
 #pragma unroll
-            for (int r = 0; r < R; ++r)
-                v[q * R + r] = (HIN && r >= R / 2) ? czero<V>() : row[pidx(b + r * LR)];
+            for (int r = 0; r < R; ++r) {
+                if (HIN && r >= R / 2) { v[q * R + r] = czero<V>(); continue; }
+                v[q * R + r] = row[(LR & 7) ? pidx(b + r * LR) : p0 + r * ld9];
+            }
             if (Ns > 1) {
-                const int k = b & (Ns - 1);
-                const int step = (L / (Ns * R)) * k * ts;
+                const int step = tstep0 * (b & (Ns - 1));
+                int t = step;
 #pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    const V w = tw[r * step];
+                for (int r = 1; r < R; ++r, t += step) {
+                    const V w = tw[t];
                     v[q * R + r] = INV ? cmulc(v[q * R + r], w) : cmul(v[q * R + r], w);
                 }
             }
@@ -136,9 +148,13 @@ __device__ __forceinline__ void stockham_pass(V *row, int L, int Ns, int j, int 
         for (int q = 0; q < NB; ++q) {
             const int b = j + q * G;
             const int k = b & (Ns - 1);
-            const int base = (b - k) * R + k;
+            const int hi = (b - k) * R;                  // multiple of 8 when R == 8
+            const int s0 = (R == 8) ? hi + (hi >> 3) + k + (k >> 3) : 0;
 #pragma unroll
-            for (int r = 0; r < (HOUT ? R / 2 : R); ++r) row[pidx(base + r * Ns)] = v[q * R + r];
+            for (int r = 0; r < (HOUT ? R / 2 : R); ++r) {
+                const int rn = r * Ns;
+                row[(R == 8) ? s0 + rn + (rn >> 3) : pidx(hi + k + rn)] = v[q * R + r];
+            }
         }
     }
     __syncthreads();
@@ -150,9 +166,15 @@ __device__ __forceinline__ void stockham_pass(V *row, int L, int Ns, int j, int 
 // of the row's group works on it.  Threads with active == false (padding
 // threads of the CTA) only take part in the barriers.  The caller
 // synchronises before the call so that the row's contents are visible; the
-// row is final after return.
-template <bool INV, bool HIN, bool HOUT, typename V>
-__device__ __forceinline__ void fft_row(V *row, int L, int logL, int j, const V *__restrict__ tw, int ts, bool active)
+// row is final after return.  Twiddles: tw[t * TS] = exp(-2 pi i t / L).
+//
+// fft_row_n takes L at run time; fft_row_c<LOGL> is the same sequence of
+// passes with L a compile-time constant, so that every offset, stride and
+// pass count folds into the instructions.  Kernels are instantiated for the
+// common lengths (template parameter LC of fft_row) and the host launches
+// the matching instance.
+template <bool INV, bool HIN, bool HOUT, int TS, typename V>
+__device__ __forceinline__ void fft_row_n(V *row, int L, int logL, int j, const V *__restrict__ tw, bool active)
 {
     if (L == 1) return;
     if (L < 8) {
@@ -190,25 +212,60 @@ __device__ __forceinline__ void fft_row(V *row, int L, int logL, int j, const V 
     int Ns = 1;
     bool first = true;
     if (rem == 1) {
-        stockham_pass<2, INV, HIN, false>(row, L, Ns, j, G, tw, ts, active);
+        stockham_pass<2, INV, HIN, false>(row, L, Ns, j, G, tw, TS, active);
         Ns = 2; first = false;
     } else if (rem == 2) {
-        stockham_pass<4, INV, HIN, false>(row, L, Ns, j, G, tw, ts, active);
+        stockham_pass<4, INV, HIN, false>(row, L, Ns, j, G, tw, TS, active);
         Ns = 4; first = false;
     }
     for (int p = 0; p < n8; ++p) {
         const bool last = (p == n8 - 1);
         if (first && HIN) {
-            if (last && HOUT) stockham_pass<8, INV, true, true>(row, L, Ns, j, G, tw, ts, active);
-            else stockham_pass<8, INV, true, false>(row, L, Ns, j, G, tw, ts, active);
+            if (last && HOUT) stockham_pass<8, INV, true, true>(row, L, Ns, j, G, tw, TS, active);
+            else stockham_pass<8, INV, true, false>(row, L, Ns, j, G, tw, TS, active);
         } else {
-            if (last && HOUT) stockham_pass<8, INV, false, true>(row, L, Ns, j, G, tw, ts, active);
-            else stockham_pass<8, INV, false, false>(row, L, Ns, j, G, tw, ts, active);
+            if (last && HOUT) stockham_pass<8, INV, false, true>(row, L, Ns, j, G, tw, TS, active);
+            else stockham_pass<8, INV, false, false>(row, L, Ns, j, G, tw, TS, active);
         }
         Ns <<= 3;
         first = false;
     }
 }
+
+template <int LOGL, bool INV, bool HIN, bool HOUT, int TS, typename V>
+__device__ __forceinline__ void fft_row_c(V *row, int j, const V *__restrict__ tw, bool active)
+{
+    static_assert(LOGL >= 3, "compile-time rows have at least 8 elements");
+    constexpr int L = 1 << LOGL, G = L >> 3, rem = LOGL % 3, n8 = LOGL / 3;
+    constexpr int NS0 = rem == 1 ? 2 : (rem == 2 ? 4 : 1);
+    if constexpr (rem == 1) stockham_pass<2, INV, HIN, false>(row, L, 1, j, G, tw, TS, active);
+    if constexpr (rem == 2) stockham_pass<4, INV, HIN, false>(row, L, 1, j, G, tw, TS, active);
+#pragma unroll
+    for (int p = 0; p < n8; ++p) {
+        const int Ns = NS0 << (3 * p);
+        const bool last = (p == n8 - 1), first = (p == 0 && rem == 0);
+        if (first && HIN) {
+            if (last && HOUT) stockham_pass<8, INV, true, true>(row, L, Ns, j, G, tw, TS, active);
+            else stockham_pass<8, INV, true, false>(row, L, Ns, j, G, tw, TS, active);
+        } else {
+            if (last && HOUT) stockham_pass<8, INV, false, true>(row, L, Ns, j, G, tw, TS, active);
+            else stockham_pass<8, INV, false, false>(row, L, Ns, j, G, tw, TS, active);
+        }
+    }
+}
+
+// LC > 0: the kernel was compiled for rows of length 2^LC (L, logL unused);
+// LC == 0: any length
+template <bool INV, bool HIN, bool HOUT, int TS, int LC, typename V>
+__device__ __forceinline__ void fft_row(V *row, int L, int logL, int j, const V *__restrict__ tw, bool active)
+{
+    if constexpr (LC > 0) fft_row_c<LC, INV, HIN, HOUT, TS>(row, j, tw, active);
+    else fft_row_n<INV, HIN, HOUT, TS>(row, L, logL, j, tw, active);
+}
+
+// Row lengths with compiled specialisations in the field kernels (log2 of
+// 64 .. 1024); other lengths take the generic code.
+#define MM_FFT_SPECIALISED(logL) ((logL) >= 6 && (logL) <= 10)
 
 // Small in-register DFT of length PZ (1, 2, 4 or 8) for the z direction,
 // with the same half-input / half-output pruning flags.

@@ -65,7 +65,7 @@ template <int PZ, bool INV, typename V> __device__ __forceinline__ V tw_pz(V v, 
 // ---------------------------------------------------------------------------
 // k_xfwd
 // ---------------------------------------------------------------------------
-template <typename T, bool MIN>
+template <typename T, bool MIN, int LX>
 __global__ void __launch_bounds__(768) k_xfwd(Geom g, FieldPtrs<T> P)
 {
     typedef typename cvec<T>::type V;
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(768) k_xfwd(Geom g, FieldPtrs<T> P)
             src = cur ? P.mbuf[0] : P.mbuf[1];
             dst = cur ? P.mbuf[1] : P.mbuf[0];
             gp = ((k - 1) & 1) ? P.gbuf[1] : P.gbuf[0];
-            tau = (T)st->tau;
+            tau = pick<T>(st->tau, st->tauf);
             step_kind = st->step_kind;
         } else {
             src = cur ? P.mbuf[1] : P.mbuf[0];
@@ -99,16 +99,16 @@ __global__ void __launch_bounds__(768) k_xfwd(Geom g, FieldPtrs<T> P)
     } else {
         src = P.m_src;
     }
-
     // load (and step) the tile; row (c, yl) holds Px reals
+#pragma unroll(sizeof(T) == 4 ? 2 : 1)
     for (int e = tid; e < TY * nx; e += nth) {
-        const int yl = e / nx, x = e - yl * nx, y = y0 + yl;
+        const int yl = g.fd_nx.div(e), x = e - yl * nx, y = y0 + yl;
         T m0 = 0, m1 = 0, m2 = 0;
         if (y < ny) {
             const long n = ((long)z * ny + y) * nx + x;
-            m0 = src[n]; m1 = src[N + n]; m2 = src[2 * N + n];
+            m0 = __ldg(src + n); m1 = __ldg(src + N + n); m2 = __ldg(src + 2 * N + n);
             if (MIN && dst) {
-                const T g0 = gp[n], g1 = gp[N + n], g2 = gp[2 * N + n];
+                const T g0 = __ldg(gp + n), g1 = __ldg(gp + N + n), g2 = __ldg(gp + 2 * N + n);
                 if (step_kind == MM_STEP_CAYLEY) {
                     const T q = (T)0.25 * tau * tau * (g0 * g0 + g1 * g1 + g2 * g2);
                     const T a = (T)1 - q, inv = (T)1 / ((T)1 + q);
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(768) k_xfwd(Geom g, FieldPtrs<T> P)
     }
     const int npad = Px - nx;
     for (int e = tid; e < 3 * TY * npad; e += nth) {
-        const int row = e / npad, x = nx + (e - row * npad);
+        const int row = g.fd_padx.div(e), x = nx + (e - row * npad);
         rel<T>(S + row * g.rsx, x) = 0;
     }
     __syncthreads();
@@ -146,13 +146,13 @@ __global__ void __launch_bounds__(768) k_xfwd(Geom g, FieldPtrs<T> P)
     {
         const int row = tid / g.Gx, j = tid - row * g.Gx;
         const bool act = row < 3 * TY;
-        fft_row<false, true, false>(S + (act ? row : 0) * g.rsx, g.Hx, g.lhx, j, tw, 2, act);
+        fft_row<false, true, false, 2, LX>(S + (act ? row : 0) * g.rsx, g.Hx, g.lhx, j, tw, act);
     }
 
     // unpack to the real-input spectrum X[k], k = 0..Hx, and store transposed
     const int Hx = g.Hx, C = g.C;
     for (int e = tid; e < TY * 3 * C; e += nth) {
-        const int c = e % 3, rest = e / 3, yl = rest % TY, k = rest / TY;
+        const int c = e % 3, rest = e / 3, yl = rest & (TY - 1), k = rest >> g.lty;
         const int y = y0 + yl;
         const V *row = S + (c * TY + yl) * g.rsx;
         const V Zk = row[pidx(k == Hx ? 0 : k)];
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(768) k_xfwd(Geom g, FieldPtrs<T> P)
 // doubles live); the y rows are then transformed in batches of RB rows
 template <typename T> struct YZBound { static constexpr int v = sizeof(T) == 8 ? 512 : 768; };
 
-template <typename T, int PZ>
+template <typename T, int PZ, int LY>
 __global__ void __launch_bounds__(YZBound<T>::v) k_yz(Geom g, FieldPtrs<T> P)
 {
     typedef typename cvec<T>::type V;
@@ -189,20 +189,21 @@ __global__ void __launch_bounds__(YZBound<T>::v) k_yz(Geom g, FieldPtrs<T> P)
     V *tw = S + nrow * g.rsy;  // Py twiddles
     load_twiddles(tw, P.tw_py, Py);
 
+#pragma unroll(sizeof(T) == 4 ? 4 : 1)
     for (int e = tid; e < nrow * ny; e += nth) {  // Wk[z][y][c] -> row (c, z)
-        const int c = e % 3, rest = e / 3, zz = rest / ny, y = rest - zz * ny;
-        S[(c * nz + zz) * g.rsy + pidx(y)] = Wk[e];
+        const int c = e % 3, rest = e / 3, zz = g.fd_ny.div(rest), y = rest - zz * ny;
+        S[(c * nz + zz) * g.rsy + pidx(y)] = __ldcg(Wk + e);
     }
     const int npad = Py - ny;
     for (int e = tid; e < nrow * npad; e += nth) {
-        const int row = e / npad, y = ny + (e - row * npad);
+        const int row = g.fd_pady.div(e), y = ny + (e - row * npad);
         S[row * g.rsy + pidx(y)] = czero<V>();
     }
     __syncthreads();
     const int rb = tid / g.Gy, j = tid - rb * g.Gy;  // row within a batch of g.RB rows
     const bool act = rb < g.RB;
     for (int r0 = 0; r0 < nrow; r0 += g.RB)
-        fft_row<false, true, false>(S + (act ? r0 + rb : 0) * g.rsy, Py, g.lpy, j, tw, 1, act);
+        fft_row<false, true, false, 1, LY>(S + (act ? r0 + rb : 0) * g.rsy, Py, g.lpy, j, tw, act);
 
     // per ky: z transform, tensor product, inverse z transform.  The z input
     // has nz <= PZ/2 non-zero values and only nz outputs are kept, so the
@@ -263,10 +264,10 @@ __global__ void __launch_bounds__(YZBound<T>::v) k_yz(Geom g, FieldPtrs<T> P)
     }
     __syncthreads();
     for (int r0 = 0; r0 < nrow; r0 += g.RB)
-        fft_row<true, false, true>(S + (act ? r0 + rb : 0) * g.rsy, Py, g.lpy, j, tw, 1, act);
+        fft_row<true, false, true, 1, LY>(S + (act ? r0 + rb : 0) * g.rsy, Py, g.lpy, j, tw, act);
 
     for (int e = tid; e < nrow * ny; e += nth) {
-        const int c = e % 3, rest = e / 3, zz = rest / ny, y = rest - zz * ny;
+        const int c = e % 3, rest = e / 3, zz = g.fd_ny.div(rest), y = rest - zz * ny;
         Wk[e] = S[(c * nz + zz) * g.rsy + pidx(y)];
     }
 }
@@ -387,6 +388,7 @@ __device__ void finish_iteration(const Geom &g, double *partials, int nblk, MinS
             if (!(isfinite(tau) && tau > 0.0)) tau = st->tau0;
         }
         st->tau = tau;
+        st->tauf = (float)tau;
         st->k = k + 1;
         stop = 0;
     }
@@ -396,7 +398,7 @@ __device__ void finish_iteration(const Geom &g, double *partials, int nblk, MinS
 // ---------------------------------------------------------------------------
 // k_xinv
 // ---------------------------------------------------------------------------
-template <typename T, int MODE>
+template <typename T, int MODE, int LX>
 __global__ void __launch_bounds__(768) k_xinv(Geom g, FieldPtrs<T> P, double hx0, double hx1, double hx2,
                                               cudaGraphConditionalHandle h, int use_cond)
 {
@@ -408,63 +410,76 @@ __global__ void __launch_bounds__(768) k_xinv(Geom g, FieldPtrs<T> P, double hx0
     const int nx = g.nx, ny = g.ny, nz = g.nz, Hx = g.Hx;
     const long N = g.N;
     V *tw = S + 3 * TY * g.rsx;
+
+    MinState *st = P.st;
+    long k = 0;
+    int cur = 0;
+    const T *m;
+    const T *mp = nullptr, *gq = nullptr;
+    if (MODE == MODE_MIN) {
+        k = st->k;
+        cur = st->base ^ (int)(k & 1);
+        m = cur ? P.mbuf[1] : P.mbuf[0];
+        mp = cur ? P.mbuf[0] : P.mbuf[1];
+        gq = (k & 1) ? P.gbuf[0] : P.gbuf[1];  // g_{k-1}
+    } else {
+        m = P.m_src;
+    }
     load_twiddles(tw, P.tw_px, g.Px);
     __syncthreads();
 
     // complex-to-real preprocessing: Z[k] = (X[k] + X*[Hx-k]) + i conj(w^k) (X[k] - X*[Hx-k])
+#pragma unroll(sizeof(T) == 4 ? 4 : 1)
     for (int e = tid; e < TY * 3 * Hx; e += nth) {
-        const int c = e % 3, rest = e / 3, yl = rest % TY, k = rest / TY;
+        const int c = e % 3, rest = e / 3, yl = rest & (TY - 1), kk = rest >> g.lty;
         const int y = y0 + yl;
         V Z = czero<V>();
         if (y < ny) {
             const long base = ((long)z * ny + y) * 3 + c;
             const long strideK = (long)3 * nz * ny;
-            const V Xk = P.W[(long)k * strideK + base];
-            const V Xm = cconj(P.W[(long)(Hx - k) * strideK + base]);
+            const V Xk = __ldg(P.W + (long)kk * strideK + base);
+            const V Xm = cconj(__ldg(P.W + (long)(Hx - kk) * strideK + base));
             const V sum = cadd(Xk, Xm), dif = csub(Xk, Xm);
-            const V t = cmulc(dif, tw[k]);  // conj(w^k) dif
+            const V t = cmulc(dif, tw[kk]);  // conj(w^k) dif
             Z.x = sum.x - t.y;
             Z.y = sum.y + t.x;
         }
-        S[(c * TY + yl) * g.rsx + pidx(k)] = Z;
+        S[(c * TY + yl) * g.rsx + pidx(kk)] = Z;
     }
     __syncthreads();
     {
         const int row = tid / g.Gx, j = tid - row * g.Gx;
         const bool act = row < 3 * TY;
-        fft_row<true, false, true>(S + (act ? row : 0) * g.rsx, Hx, g.lhx, j, tw, 2, act);
+        fft_row<true, false, true, 2, LX>(S + (act ? row : 0) * g.rsx, Hx, g.lhx, j, tw, act);
     }
 
     // local terms
-    MinState *st = P.st;
-    long k = 0;
-    int cur = 0;
-    const T *m;
+    T he0, he1, he2;
     if (MODE == MODE_MIN) {
-        k = st->k;
-        cur = st->base ^ (int)(k & 1);
-        m = cur ? P.mbuf[1] : P.mbuf[0];
-        hx0 = st->Hext[0]; hx1 = st->Hext[1]; hx2 = st->Hext[2];
+        he0 = pick<T>(st->Hext[0], st->Hextf[0]);
+        he1 = pick<T>(st->Hext[1], st->Hextf[1]);
+        he2 = pick<T>(st->Hext[2], st->Hextf[2]);
     } else {
-        m = P.m_src;
+        he0 = (T)hx0; he1 = (T)hx1; he2 = (T)hx2;
     }
-    const T he0 = (T)hx0, he1 = (T)hx1, he2 = (T)hx2;
-    const T cx = (T)g.cex_x, cy = (T)g.cex_y, cz = (T)g.cex_z, can = (T)g.can;
-    const T kfac = (T)(0.5 * g.can);  // 1/(mu0 Ms)
-    const T Kuni = (T)g.K, ux = (T)g.u[0], uy = (T)g.u[1], uz = (T)g.u[2];  // converted once, not per cell
+    const T cx = pick<T>(g.cex_x, g.fcex_x), cy = pick<T>(g.cex_y, g.fcex_y), cz = pick<T>(g.cex_z, g.fcex_z);
+    const T can = pick<T>(g.can, g.fcan);
+    const T kfac = (T)0.5 * can;  // 1/(mu0 Ms)
+    const T Kuni = pick<T>(g.K, g.fK), ux = pick<T>(g.u[0], g.fu[0]), uy = pick<T>(g.u[1], g.fu[1]),
+            uz = pick<T>(g.u[2], g.fu[2]);
     const T hs = (T)P.hscale;
     Acc<T> red[NSL];
 #pragma unroll
     for (int s = 0; s < NSL; ++s) red[s].zero();
 
     for (int e = tid; e < TY * nx; e += nth) {
-        const int yl = e / nx, x = e - yl * nx, y = y0 + yl;
+        const int yl = g.fd_nx.div(e), x = e - yl * nx, y = y0 + yl;
         if (y >= ny) continue;
         const long n = ((long)z * ny + y) * nx + x;
         const T d0 = rel<T>(S + (0 * TY + yl) * g.rsx, x);
         const T d1 = rel<T>(S + (1 * TY + yl) * g.rsx, x);
         const T d2 = rel<T>(S + (2 * TY + yl) * g.rsx, x);
-        const T m0 = m[n], m1 = m[N + n], m2 = m[2 * N + n];
+        const T m0 = __ldg(m + n), m1 = __ldg(m + N + n), m2 = __ldg(m + 2 * N + n);
         // exchange: sum over present neighbours of (m_j - m_i) / d^2 (free faces)
         T e0 = 0, e1 = 0, e2 = 0;
         if (x > 0)      { e0 += cx * (m[n - 1] - m0);  e1 += cx * (m[N + n - 1] - m1);  e2 += cx * (m[2 * N + n - 1] - m2); }
@@ -508,10 +523,10 @@ __global__ void __launch_bounds__(768) k_xinv(Geom g, FieldPtrs<T> P, double hx0
         red[SL_ET].add((T)-0.5 * (mh + mhe) + kfac * Kv);
         T *gout = (k & 1) ? P.gbuf[1] : P.gbuf[0];
         if (k > 0) {
-            const T *mp = cur ? P.mbuf[0] : P.mbuf[1];
-            const T *gq = (k & 1) ? P.gbuf[0] : P.gbuf[1];  // g_{k-1}
-            const T s0 = m0 - mp[n], s1 = m1 - mp[N + n], s2 = m2 - mp[2 * N + n];
-            const T y0v = g0 - gq[n], y1v = g1 - gq[N + n], y2v = g2 - gq[2 * N + n];
+            const T p0 = mp[n], p1 = mp[N + n], p2 = mp[2 * N + n];
+            const T q0 = gq[n], q1 = gq[N + n], q2 = gq[2 * N + n];
+            const T s0 = m0 - p0, s1 = m1 - p1, s2 = m2 - p2;
+            const T y0v = g0 - q0, y1v = g1 - q1, y2v = g2 - q2;
             red[SL_SS].add(s0 * s0 + s1 * s1 + s2 * s2);
             red[SL_SY].add(s0 * y0v + s1 * y1v + s2 * y2v);
             red[SL_YY].add(y0v * y0v + y1v * y1v + y2v * y2v);
@@ -568,9 +583,10 @@ __global__ void k_init_state(MinState *st, double tau0, double tol_abs, double h
     else st->base = st->base ^ (int)(st->k & 1);   // continue from the previous result
     st->tau0 = tau0; st->tol_abs = tol_abs;
     st->Hext[0] = h0; st->Hext[1] = h1; st->Hext[2] = h2;
+    st->Hextf[0] = (float)h0; st->Hextf[1] = (float)h1; st->Hextf[2] = (float)h2;
     st->max_iter = max_iter; st->step_kind = step_kind;
     st->timeout_ns = timeout_ns; st->t_start_ns = 0;
-    st->k = 0; st->tau = tau0; st->status = MMS_RUNNING; st->evals = 0; st->launches = 1;
+    st->k = 0; st->tau = tau0; st->tauf = (float)tau0; st->status = MMS_RUNNING; st->evals = 0; st->launches = 1;
     st->max_torque = 0;
 }
 
@@ -636,7 +652,7 @@ template <typename T> int threads_yz(const Geom &g) { return round32(g.RB * g.Gy
 template <typename T> size_t smem_x_t(const Geom &g)
 {
     typedef typename cvec<T>::type V;
-    const size_t rows = (size_t)3 * g.TY * g.rsx * sizeof(V) + (size_t)g.Px * sizeof(V);
+    size_t rows = (size_t)3 * g.TY * g.rsx * sizeof(V) + (size_t)g.Px * sizeof(V);
     const size_t stage = (size_t)NSL * threads_x<T>(g) * sizeof(Acc<T>);
     return rows > stage ? rows : stage;
 }
@@ -646,10 +662,50 @@ template <typename T> size_t smem_yz_t(const Geom &g)
     return (size_t)3 * g.nz * g.rsy * sizeof(V) + (size_t)g.Py * sizeof(V);
 }
 
+// The field kernels are compiled for FFT row lengths 2^6 .. 2^10 (template
+// parameter LX of the x kernels: log2 Hx; LY of the y-z kernel: log2 Py) and
+// once for any length (0); these launchers pick the instance.
+inline int lc_of(int logL) { return MM_FFT_SPECIALISED(logL) ? logL : 0; }
+#define MM_LC_CASES(X) X(0) X(6) X(7) X(8) X(9) X(10)
+
+template <typename T, bool MIN>
+cudaError_t launch_xfwd(const Geom &g, const FieldPtrs<T> &P, cudaStream_t s)
+{
+    const dim3 grid((g.ny + g.TY - 1) / g.TY, g.nz);
+    const int thr = threads_x<T>(g);
+    const size_t sm = smem_x_t<T>(g);
+    switch (lc_of(g.lhx)) {
+#define C(L) case L: k_xfwd<T, MIN, L><<<grid, thr, sm, s>>>(g, P); break;
+        MM_LC_CASES(C)
+#undef C
+    }
+    return cudaGetLastError();
+}
+
+template <typename T, int MODE>
+cudaError_t launch_xinv(const Geom &g, const FieldPtrs<T> &P, cudaStream_t s, const double *hext,
+                        cudaGraphConditionalHandle h, int use_cond)
+{
+    const dim3 grid((g.ny + g.TY - 1) / g.TY, g.nz);
+    const int thr = threads_x<T>(g);
+    const size_t sm = smem_x_t<T>(g);
+    const double h0 = hext ? hext[0] : 0.0, h1 = hext ? hext[1] : 0.0, h2 = hext ? hext[2] : 0.0;
+    switch (lc_of(g.lhx)) {
+#define C(L) case L: k_xinv<T, MODE, L><<<grid, thr, sm, s>>>(g, P, h0, h1, h2, h, use_cond); break;
+        MM_LC_CASES(C)
+#undef C
+    }
+    return cudaGetLastError();
+}
+
 template <typename T, int PZ>
 cudaError_t launch_yz(const Geom &g, const FieldPtrs<T> &P, cudaStream_t s)
 {
-    k_yz<T, PZ><<<g.C, threads_yz<T>(g), smem_yz_t<T>(g), s>>>(g, P);
+    switch (lc_of(g.lpy)) {
+#define C(L) case L: k_yz<T, PZ, L><<<g.C, threads_yz<T>(g), smem_yz_t<T>(g), s>>>(g, P); break;
+        MM_LC_CASES(C)
+#undef C
+    }
     return cudaGetLastError();
 }
 
@@ -658,10 +714,9 @@ cudaError_t launch_yz_any(const Geom &g, const FieldPtrs<T> &P, cudaStream_t s)
 {
     switch (g.Pz) {
     case 1: return launch_yz<T, 1>(g, P, s);
-    case 2: return launch_yz<T, 2>(g, P, s);
     case 4: return launch_yz<T, 4>(g, P, s);
     case 8: return launch_yz<T, 8>(g, P, s);
-    default: return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;  // Pz = 2 does not occur (nz = 1 gives 1, nz = 2 gives 4)
     }
 }
 
@@ -672,25 +727,36 @@ cudaError_t launch_conv(const Geom &g, const FieldPtrs<T> &P, cudaStream_t s)
     return g.bulk ? mm_bulk_conv(g, P, s, -1) : launch_yz_any<T>(g, P, s);
 }
 
-template <typename T, int PZ> cudaError_t set_yz_attr(size_t smem)
+template <typename F> cudaError_t smem_attr(F *f, size_t bytes)
 {
-    return cudaFuncSetAttribute(k_yz<T, PZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <typename T> cudaError_t configure_t(size_t sx, size_t syz, int Pz, int bulk)
+// dynamic shared memory limits of the instances this geometry launches
+template <typename T> cudaError_t configure_t(const Geom &g, size_t sx, size_t syz)
 {
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_xfwd<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx))) return e;
-    if ((e = cudaFuncSetAttribute(k_xfwd<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx))) return e;
-    if ((e = cudaFuncSetAttribute(k_xinv<T, MODE_HEFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx))) return e;
-    if ((e = cudaFuncSetAttribute(k_xinv<T, MODE_ENERGY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx))) return e;
-    if ((e = cudaFuncSetAttribute(k_xinv<T, MODE_MIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx))) return e;
-    if (bulk) return cudaSuccess;
-    switch (Pz) {
-    case 1: return set_yz_attr<T, 1>(syz);
-    case 2: return set_yz_attr<T, 2>(syz);
-    case 4: return set_yz_attr<T, 4>(syz);
-    case 8: return set_yz_attr<T, 8>(syz);
+    cudaError_t e = cudaSuccess;
+    switch (lc_of(g.lhx)) {
+#define C(L)                                                                                     \
+    case L:                                                                                      \
+        if ((e = smem_attr(k_xfwd<T, false, L>, sx)) || (e = smem_attr(k_xfwd<T, true, L>, sx)) || \
+            (e = smem_attr(k_xinv<T, MODE_HEFF, L>, sx)) || (e = smem_attr(k_xinv<T, MODE_ENERGY, L>, sx)) || \
+            (e = smem_attr(k_xinv<T, MODE_MIN, L>, sx)))                                         \
+            return e;                                                                            \
+        break;
+        MM_LC_CASES(C)
+#undef C
+    }
+    if (g.bulk) return cudaSuccess;
+    switch (lc_of(g.lpy)) {
+#define C(L)                                                                                     \
+    case L:                                                                                      \
+        if (g.Pz == 1) return smem_attr(k_yz<T, 1, L>, syz);                                     \
+        if (g.Pz == 4) return smem_attr(k_yz<T, 4, L>, syz);                                     \
+        if (g.Pz == 8) return smem_attr(k_yz<T, 8, L>, syz);                                     \
+        return cudaErrorInvalidValue;
+        MM_LC_CASES(C)
+#undef C
     }
     return cudaErrorInvalidValue;
 }
@@ -714,13 +780,12 @@ template <typename T> cudaError_t autotune_t(mm_problem *p, const int *tys, int 
     int bty = tys[0];
     for (int i = 0; i < nty && !e; ++i) {
         g.TY = tys[i];
-        const dim3 gx((g.ny + g.TY - 1) / g.TY, g.nz);
-        const size_t sx = smem_x_t<T>(g);
+        g.lty = mm_ilog2(g.TY);
         float tmin = 1e30f;
         for (int r = 0; r < 3 && !e; ++r) {
             cudaEventRecord(a, s);
-            k_xfwd<T, false><<<gx, threads_x<T>(g), sx, s>>>(g, P);
-            k_xinv<T, MODE_HEFF><<<gx, threads_x<T>(g), sx, s>>>(g, P, 0.0, 0.0, 0.0, 0, 0);
+            launch_xfwd<T, false>(g, P, s);
+            launch_xinv<T, MODE_HEFF>(g, P, s, nullptr, 0, 0);
             cudaEventRecord(b, s);
             if ((e = cudaGetLastError()) || (e = cudaEventSynchronize(b))) break;
             float t = 0;
@@ -730,6 +795,7 @@ template <typename T> cudaError_t autotune_t(mm_problem *p, const int *tys, int 
         if (tmin < best) { best = tmin; bty = tys[i]; }
     }
     g.TY = bty;
+    g.lty = mm_ilog2(g.TY);
     best = 1e30f;
     int brb = rbs[0];
     for (int i = 0; i < nrb && !e && !g.bulk; ++i) {
@@ -763,17 +829,11 @@ cudaError_t heff_chain_t(mm_problem *p, const void *m, void *H, const double *he
     P.m_src = (const T *)m;
     P.H_out = (T *)H;
     P.hscale = hscale;
-    const dim3 gx((g.ny + g.TY - 1) / g.TY, g.nz);
-    const size_t sx = smem_x_t<T>(g);
-    k_xfwd<T, false><<<gx, threads_x<T>(g), sx, s>>>(g, P);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_xfwd<T, false>(g, P, s);
     if (e) return e;
     if ((e = launch_conv<T>(g, P, s))) return e;
-    if (mode == MODE_HEFF)
-        k_xinv<T, MODE_HEFF><<<gx, threads_x<T>(g), sx, s>>>(g, P, hext[0], hext[1], hext[2], 0, 0);
-    else
-        k_xinv<T, MODE_ENERGY><<<gx, threads_x<T>(g), sx, s>>>(g, P, hext[0], hext[1], hext[2], 0, 0);
-    return cudaGetLastError();
+    if (mode == MODE_HEFF) return launch_xinv<T, MODE_HEFF>(g, P, s, hext, 0, 0);
+    return launch_xinv<T, MODE_ENERGY>(g, P, s, hext, 0, 0);
 }
 
 template <typename T>
@@ -781,14 +841,10 @@ cudaError_t min_body_t(mm_problem *p, cudaGraphConditionalHandle h, cudaStream_t
 {
     const Geom &g = p->g;
     FieldPtrs<T> P = make_ptrs<T>(p);
-    const dim3 gx((g.ny + g.TY - 1) / g.TY, g.nz);
-    const size_t sx = smem_x_t<T>(g);
-    k_xfwd<T, true><<<gx, threads_x<T>(g), sx, s>>>(g, P);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_xfwd<T, true>(g, P, s);
     if (e) return e;
     if ((e = launch_conv<T>(g, P, s))) return e;
-    k_xinv<T, MODE_MIN><<<gx, threads_x<T>(g), sx, s>>>(g, P, 0.0, 0.0, 0.0, h, use_cond);
-    return cudaGetLastError();
+    return launch_xinv<T, MODE_MIN>(g, P, s, nullptr, h, use_cond);
 }
 
 template <typename T>
@@ -796,8 +852,6 @@ cudaError_t stage_times_t(mm_problem *p, int reps, double *ms, cudaStream_t s)
 {
     const Geom &g = p->g;
     FieldPtrs<T> P = make_ptrs<T>(p);
-    const dim3 gx((g.ny + g.TY - 1) / g.TY, g.nz);
-    const size_t sx = smem_x_t<T>(g);
     const int nst = g.bulk ? 5 : 3;
     cudaEvent_t ev[6];
     for (int i = 0; i <= nst; ++i)
@@ -807,7 +861,7 @@ cudaError_t stage_times_t(mm_problem *p, int reps, double *ms, cudaStream_t s)
     for (int r = 0; r < reps && !e; ++r) {
         int i = 0;
         cudaEventRecord(ev[i++], s);
-        k_xfwd<T, true><<<gx, threads_x<T>(g), sx, s>>>(g, P);
+        launch_xfwd<T, true>(g, P, s);
         cudaEventRecord(ev[i++], s);
         if (g.bulk) {
             for (int pass = 0; pass < 3; ++pass) {
@@ -818,7 +872,7 @@ cudaError_t stage_times_t(mm_problem *p, int reps, double *ms, cudaStream_t s)
             launch_yz_any<T>(g, P, s);
             cudaEventRecord(ev[i++], s);
         }
-        k_xinv<T, MODE_MIN><<<gx, threads_x<T>(g), sx, s>>>(g, P, 0.0, 0.0, 0.0, 0, 0);
+        launch_xinv<T, MODE_MIN>(g, P, s, nullptr, 0, 0);
         cudaEventRecord(ev[i++], s);
         if ((e = cudaGetLastError())) break;
         if ((e = cudaEventSynchronize(ev[nst]))) break;
@@ -857,8 +911,7 @@ int mm_yz_thread_bound(const mm_problem *p) { return DISPATCH(p, YZBound<double>
 int mm_heff_configure(mm_problem *p, size_t sx_max)
 {
     const size_t syz = p->g.bulk ? 0 : mm_smem_yz_for(p);
-    cudaError_t e = DISPATCH(p, configure_t<double>(sx_max, syz, p->g.Pz, p->g.bulk),
-                             configure_t<float>(sx_max, syz, p->g.Pz, p->g.bulk));
+    cudaError_t e = DISPATCH(p, configure_t<double>(p->g, sx_max, syz), configure_t<float>(p->g, sx_max, syz));
     if (!e && p->g.bulk) e = mm_bulk_configure(p);
     if (e) { mm_set_cuda_error(e, "cudaFuncSetAttribute"); return MM_ERR_CUDA; }
     return MM_OK;

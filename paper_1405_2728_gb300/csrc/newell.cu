@@ -128,7 +128,7 @@ __global__ void k_fft_strided(double2 *F, int L, int logL, long stride, long inn
     __syncthreads();
     const int G = L >= 8 ? L / 8 : 1;
     const bool act = threadIdx.x < G;
-    fft_row<false, false, false>(S, L, logL, act ? (int)threadIdx.x : 0, tw, 1, act);
+    fft_row<false, false, false, 1, 0>(S, L, logL, act ? (int)threadIdx.x : 0, tw, act);
     __syncthreads();
     for (int t = threadIdx.x; t < L; t += blockDim.x) F[base + t * stride] = S[pidx(t)];
 }
