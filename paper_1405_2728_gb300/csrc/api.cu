@@ -132,6 +132,9 @@ int plan(mm_problem *p)
     g.fd_nx.init(gr.nx); g.fd_ny.init(gr.ny);
     g.fd_padx.init(g.Px - gr.nx > 0 ? g.Px - gr.nx : 1);
     g.fd_pady.init(g.Py - gr.ny > 0 ? g.Py - gr.ny : 1);
+    // the float x-inverse kernel stages its stencil rows with 16-byte copies
+    g.stage = p->precision == MM_FP32 && gr.nx % 4 == 0;
+    g.fd_nc.init(g.stage ? gr.nx / 4 : 1);
     if (g.Px > 4096 || g.Py > 4096 || g.Pz > 4096) return MM_ERR_UNSUPPORTED;
     // padded shared-memory rows (one pad element per 8, see fft.cuh)
     g.rsx = padded_row(g.Hx);

@@ -141,6 +141,8 @@ struct Geom {
     float fcex_x, fcex_y, fcex_z, fcan, fK, fu[3];
     int lty;                       // log2(TY)
     FastDiv fd_nx, fd_ny, fd_padx, fd_pady;  // divisors nx, ny, Px - nx, Py - ny
+    int stage;                     // k_xinv (float) stages its stencil rows with 16-byte cp.async
+    FastDiv fd_nc;                 // 16-byte chunks per x row when staging
 };
 
 __host__ __device__ __forceinline__ int mm_ilog2(int v)
@@ -149,6 +151,28 @@ __host__ __device__ __forceinline__ int mm_ilog2(int v)
     while ((1 << l) < v) ++l;
     return l;
 }
+
+#ifdef __CUDACC__
+// asynchronous global -> shared copies (cp.async); both addresses aligned to
+// the copy size; complete for the issuing thread at cp_async_wait_all()
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most N of this thread's most recent commit groups are pending
+template <int N> __device__ __forceinline__ void cp_async_wait_group()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+#endif
 
 // value of a double constant in the kernel's precision (float copy for float)
 template <typename T> __host__ __device__ __forceinline__ T pick(double d, float f)

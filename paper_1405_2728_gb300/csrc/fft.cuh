@@ -35,6 +35,16 @@ template <typename V> __device__ __forceinline__ void load_twiddles(V *dst, cons
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
+// the same, issued as asynchronous copies (8 or 16 bytes per element);
+// complete at cp_async_wait_all() of each thread, then a barrier
+template <typename V> __device__ __forceinline__ void load_twiddles_async(V *dst, const V *src, int n)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        if constexpr (sizeof(V) == 16) cp_async16(dst + i, src + i);
+        else cp_async8(dst + i, src + i);
+    }
+}
+
 // 2-point DFT
 template <bool HIN, typename V> __device__ __forceinline__ void dft2(V &a0, V &a1)
 {

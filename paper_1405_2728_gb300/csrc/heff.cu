@@ -62,6 +62,33 @@ template <int PZ, bool INV, typename V> __device__ __forceinline__ V tw_pz(V v, 
     return o;
 }
 
+// Rows of a field [3][nz][ny][nx] copied asynchronously into shared memory:
+// dst [3][nrows][nx] receives rows y = ylo .. ylo + nrows - 1 of plane z
+// (rows outside 0..ny-1 are skipped) in 16-byte chunks (the planner checked
+// that rows start on 16-byte boundaries).
+template <typename T>
+__device__ __forceinline__ void stage_rows(T *dst, const T *__restrict__ src, const Geom &g, int z, int ylo,
+                                           int nrows)
+{
+    constexpr int CH = 16 / sizeof(T);
+    const int nx = g.nx, nc = g.fd_nc.d;
+    const int tot = 3 * nrows * nc;
+    const long plane = (long)z * g.ny * nx;
+    for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+        const int rr = g.fd_nc.div(q), ch = q - rr * nc;  // rr = c * nrows + r
+        const int c = (rr >= nrows) + (rr >= 2 * nrows), r = rr - c * nrows, y = ylo + r;
+        if (y < 0 || y >= g.ny) continue;
+        cp_async16(dst + (long)rr * nx + ch * CH, src + c * g.N + plane + (long)y * nx + ch * CH);
+    }
+}
+
+// byte offset of the staging area of k_xinv (after the FFT rows and the
+// twiddles, 16-byte aligned); it holds (15 TY + 6) rows of nx values
+template <typename T> __host__ __device__ __forceinline__ size_t stage_offset(const Geom &g)
+{
+    return ((size_t)(3 * g.TY * g.rsx + g.Px) * 2 * sizeof(T) + 15) & ~(size_t)15;
+}
+
 // ---------------------------------------------------------------------------
 // k_xfwd
 // ---------------------------------------------------------------------------
@@ -187,18 +214,32 @@ __global__ void __launch_bounds__(YZBound<T>::v) k_yz(Geom g, FieldPtrs<T> P)
     const int nrow = 3 * nz;
     V *Wk = P.W + (long)kx * nrow * ny;
     V *tw = S + nrow * g.rsy;  // Py twiddles
-    load_twiddles(tw, P.tw_py, Py);
+    load_twiddles_async(tw, P.tw_py, Py);
 
-#pragma unroll(sizeof(T) == 4 ? 4 : 1)
-    for (int e = tid; e < nrow * ny; e += nth) {  // Wk[z][y][c] -> row (c, z)
-        const int c = e % 3, rest = e / 3, zz = g.fd_ny.div(rest), y = rest - zz * ny;
-        S[(c * nz + zz) * g.rsy + pidx(y)] = __ldcg(Wk + e);
+    // Wk[z][y][c] -> row (c, z); PF loads per thread in flight before use
+    constexpr int PF = sizeof(T) == 4 ? 8 : 4;
+    const int tot = nrow * ny;
+    for (int e0 = tid; e0 < tot; e0 += PF * nth) {
+        V v[PF];
+#pragma unroll
+        for (int i = 0; i < PF; ++i) {
+            const int e = e0 + i * nth;
+            if (e < tot) v[i] = __ldcg(Wk + e);
+        }
+#pragma unroll
+        for (int i = 0; i < PF; ++i) {
+            const int e = e0 + i * nth;
+            if (e >= tot) break;
+            const int c = e % 3, rest = e / 3, zz = g.fd_ny.div(rest), y = rest - zz * ny;
+            S[(c * nz + zz) * g.rsy + pidx(y)] = v[i];
+        }
     }
     const int npad = Py - ny;
     for (int e = tid; e < nrow * npad; e += nth) {
         const int row = g.fd_pady.div(e), y = ny + (e - row * npad);
         S[row * g.rsy + pidx(y)] = czero<V>();
     }
+    cp_async_wait_all();
     __syncthreads();
     const int rb = tid / g.Gy, j = tid - rb * g.Gy;  // row within a batch of g.RB rows
     const bool act = rb < g.RB;
@@ -425,26 +466,61 @@ __global__ void __launch_bounds__(768) k_xinv(Geom g, FieldPtrs<T> P, double hx0
     } else {
         m = P.m_src;
     }
-    load_twiddles(tw, P.tw_px, g.Px);
-    __syncthreads();
+    // the float kernel stages the local terms' inputs -- m on planes z-1, z,
+    // z+1 (rows y0-1 .. y0+TY on its own plane), m_{k-1} and g_{k-1} -- with
+    // cp.async now; they arrive while the inverse x-FFT runs
+    const bool stg = sizeof(T) == 4 && MODE == MODE_MIN && g.stage;
+    T *SG = reinterpret_cast<T *>(smem_raw + stage_offset<T>(g));
+    const int oZm = 3 * (TY + 2) * nx, oZp = oZm + 3 * TY * nx, oMP = oZp + 3 * TY * nx, oGQ = oMP + 3 * TY * nx;
+    load_twiddles_async(tw, P.tw_px, g.Px);
+    cp_async_commit();
+    if (stg) {
+        stage_rows(SG, m, g, z, y0 - 1, TY + 2);
+        if (z > 0) stage_rows(SG + oZm, m, g, z - 1, y0, TY);
+        if (z < nz - 1) stage_rows(SG + oZp, m, g, z + 1, y0, TY);
+        if (k > 0) {
+            stage_rows(SG + oMP, mp, g, z, y0, TY);
+            stage_rows(SG + oGQ, gq, g, z, y0, TY);
+        }
+    }
+    cp_async_commit();
 
-    // complex-to-real preprocessing: Z[k] = (X[k] + X*[Hx-k]) + i conj(w^k) (X[k] - X*[Hx-k])
-#pragma unroll(sizeof(T) == 4 ? 4 : 1)
-    for (int e = tid; e < TY * 3 * Hx; e += nth) {
-        const int c = e % 3, rest = e / 3, yl = rest & (TY - 1), kk = rest >> g.lty;
-        const int y = y0 + yl;
-        V Z = czero<V>();
-        if (y < ny) {
-            const long base = ((long)z * ny + y) * 3 + c;
-            const long strideK = (long)3 * nz * ny;
-            const V Xk = __ldg(P.W + (long)kk * strideK + base);
-            const V Xm = cconj(__ldg(P.W + (long)(Hx - kk) * strideK + base));
+    // complex-to-real preprocessing: Z[k] = (X[k] + X*[Hx-k]) + i conj(w^k) (X[k] - X*[Hx-k]);
+    // the spectrum loads of PF elements per thread are issued before any is used
+    constexpr int PF = sizeof(T) == 4 ? 8 : 4;
+    const int nel = TY * 3 * Hx;
+    const long strideK = (long)3 * nz * ny;
+    for (int g0 = 0; g0 < nel; g0 += PF * nth) {  // trip count uniform over the CTA (barrier inside)
+        const int e0 = g0 + tid;
+        V xa[PF], xb[PF];
+#pragma unroll
+        for (int i = 0; i < PF; ++i) {
+            const int e = e0 + i * nth;
+            const int c = e % 3, rest = e / 3, yl = rest & (TY - 1), kk = rest >> g.lty;
+            xa[i] = czero<V>(); xb[i] = czero<V>();
+            if (e < nel && y0 + yl < ny) {
+                const long base = ((long)z * ny + y0 + yl) * 3 + c;
+                xa[i] = __ldg(P.W + (long)kk * strideK + base);
+                xb[i] = __ldg(P.W + (long)(Hx - kk) * strideK + base);
+            }
+        }
+        if (g0 == 0) {  // the twiddles (first commit group) are needed from here on
+            cp_async_wait_group<1>();
+            __syncthreads();
+        }
+#pragma unroll
+        for (int i = 0; i < PF; ++i) {
+            const int e = e0 + i * nth;
+            if (e >= nel) break;
+            const int c = e % 3, rest = e / 3, yl = rest & (TY - 1), kk = rest >> g.lty;
+            const V Xk = xa[i], Xm = cconj(xb[i]);
             const V sum = cadd(Xk, Xm), dif = csub(Xk, Xm);
             const V t = cmulc(dif, tw[kk]);  // conj(w^k) dif
+            V Z;
             Z.x = sum.x - t.y;
             Z.y = sum.y + t.x;
+            S[(c * TY + yl) * g.rsx + pidx(kk)] = Z;
         }
-        S[(c * TY + yl) * g.rsx + pidx(kk)] = Z;
     }
     __syncthreads();
     {
@@ -452,6 +528,8 @@ __global__ void __launch_bounds__(768) k_xinv(Geom g, FieldPtrs<T> P, double hx0
         const bool act = row < 3 * TY;
         fft_row<true, false, true, 2, LX>(S + (act ? row : 0) * g.rsx, Hx, g.lhx, j, tw, act);
     }
+    cp_async_wait_all();
+    if (stg) __syncthreads();
 
     // local terms
     T he0, he1, he2;
@@ -479,16 +557,29 @@ __global__ void __launch_bounds__(768) k_xinv(Geom g, FieldPtrs<T> P, double hx0
         const T d0 = rel<T>(S + (0 * TY + yl) * g.rsx, x);
         const T d1 = rel<T>(S + (1 * TY + yl) * g.rsx, x);
         const T d2 = rel<T>(S + (2 * TY + yl) * g.rsx, x);
-        const T m0 = __ldg(m + n), m1 = __ldg(m + N + n), m2 = __ldg(m + 2 * N + n);
         // exchange: sum over present neighbours of (m_j - m_i) / d^2 (free faces)
-        T e0 = 0, e1 = 0, e2 = 0;
-        if (x > 0)      { e0 += cx * (m[n - 1] - m0);  e1 += cx * (m[N + n - 1] - m1);  e2 += cx * (m[2 * N + n - 1] - m2); }
-        if (x < nx - 1) { e0 += cx * (m[n + 1] - m0);  e1 += cx * (m[N + n + 1] - m1);  e2 += cx * (m[2 * N + n + 1] - m2); }
-        if (y > 0)      { e0 += cy * (m[n - nx] - m0); e1 += cy * (m[N + n - nx] - m1); e2 += cy * (m[2 * N + n - nx] - m2); }
-        if (y < ny - 1) { e0 += cy * (m[n + nx] - m0); e1 += cy * (m[N + n + nx] - m1); e2 += cy * (m[2 * N + n + nx] - m2); }
-        const long sxy = (long)nx * ny;
-        if (z > 0)      { e0 += cz * (m[n - sxy] - m0); e1 += cz * (m[N + n - sxy] - m1); e2 += cz * (m[2 * N + n - sxy] - m2); }
-        if (z < nz - 1) { e0 += cz * (m[n + sxy] - m0); e1 += cz * (m[N + n + sxy] - m1); e2 += cz * (m[2 * N + n + sxy] - m2); }
+        T m0, m1, m2, e0 = 0, e1 = 0, e2 = 0;
+        if (stg) {
+            const int cs = (TY + 2) * nx, ct = TY * nx;    // component strides of the staged rows
+            const T *r0 = SG + (yl + 1) * nx + x;          // this cell, component 0
+            m0 = r0[0]; m1 = r0[cs]; m2 = r0[2 * cs];
+            if (x > 0)      { e0 += cx * (r0[-1] - m0);  e1 += cx * (r0[cs - 1] - m1);  e2 += cx * (r0[2 * cs - 1] - m2); }
+            if (x < nx - 1) { e0 += cx * (r0[1] - m0);   e1 += cx * (r0[cs + 1] - m1);  e2 += cx * (r0[2 * cs + 1] - m2); }
+            if (y > 0)      { e0 += cy * (r0[-nx] - m0); e1 += cy * (r0[cs - nx] - m1); e2 += cy * (r0[2 * cs - nx] - m2); }
+            if (y < ny - 1) { e0 += cy * (r0[nx] - m0);  e1 += cy * (r0[cs + nx] - m1); e2 += cy * (r0[2 * cs + nx] - m2); }
+            const T *rz = SG + yl * nx + x;
+            if (z > 0)      { const T *q = rz + oZm; e0 += cz * (q[0] - m0); e1 += cz * (q[ct] - m1); e2 += cz * (q[2 * ct] - m2); }
+            if (z < nz - 1) { const T *q = rz + oZp; e0 += cz * (q[0] - m0); e1 += cz * (q[ct] - m1); e2 += cz * (q[2 * ct] - m2); }
+        } else {
+            m0 = __ldg(m + n); m1 = __ldg(m + N + n); m2 = __ldg(m + 2 * N + n);
+            if (x > 0)      { e0 += cx * (m[n - 1] - m0);  e1 += cx * (m[N + n - 1] - m1);  e2 += cx * (m[2 * N + n - 1] - m2); }
+            if (x < nx - 1) { e0 += cx * (m[n + 1] - m0);  e1 += cx * (m[N + n + 1] - m1);  e2 += cx * (m[2 * N + n + 1] - m2); }
+            if (y > 0)      { e0 += cy * (m[n - nx] - m0); e1 += cy * (m[N + n - nx] - m1); e2 += cy * (m[2 * N + n - nx] - m2); }
+            if (y < ny - 1) { e0 += cy * (m[n + nx] - m0); e1 += cy * (m[N + n + nx] - m1); e2 += cy * (m[2 * N + n + nx] - m2); }
+            const long sxy = (long)nx * ny;
+            if (z > 0)      { e0 += cz * (m[n - sxy] - m0); e1 += cz * (m[N + n - sxy] - m1); e2 += cz * (m[2 * N + n - sxy] - m2); }
+            if (z < nz - 1) { e0 += cz * (m[n + sxy] - m0); e1 += cz * (m[N + n + sxy] - m1); e2 += cz * (m[2 * N + n + sxy] - m2); }
+        }
         // uniaxial anisotropy
         const T Kv = P.Kc ? P.Kc[n] : Kuni;
         T u0, u1, u2;
@@ -523,8 +614,15 @@ __global__ void __launch_bounds__(768) k_xinv(Geom g, FieldPtrs<T> P, double hx0
         red[SL_ET].add((T)-0.5 * (mh + mhe) + kfac * Kv);
         T *gout = (k & 1) ? P.gbuf[1] : P.gbuf[0];
         if (k > 0) {
-            const T p0 = mp[n], p1 = mp[N + n], p2 = mp[2 * N + n];
-            const T q0 = gq[n], q1 = gq[N + n], q2 = gq[2 * N + n];
+            T p0, p1, p2, q0, q1, q2;
+            if (stg) {
+                const int sn = yl * nx + x, ct = TY * nx;
+                p0 = SG[oMP + sn]; p1 = SG[oMP + ct + sn]; p2 = SG[oMP + 2 * ct + sn];
+                q0 = SG[oGQ + sn]; q1 = SG[oGQ + ct + sn]; q2 = SG[oGQ + 2 * ct + sn];
+            } else {
+                p0 = mp[n]; p1 = mp[N + n]; p2 = mp[2 * N + n];
+                q0 = gq[n]; q1 = gq[N + n]; q2 = gq[2 * N + n];
+            }
             const T s0 = m0 - p0, s1 = m1 - p1, s2 = m2 - p2;
             const T y0v = g0 - q0, y1v = g1 - q1, y2v = g2 - q2;
             red[SL_SS].add(s0 * s0 + s1 * s1 + s2 * s2);
@@ -653,6 +751,7 @@ template <typename T> size_t smem_x_t(const Geom &g)
 {
     typedef typename cvec<T>::type V;
     size_t rows = (size_t)3 * g.TY * g.rsx * sizeof(V) + (size_t)g.Px * sizeof(V);
+    if (sizeof(T) == 4 && g.stage) rows = stage_offset<T>(g) + (size_t)(15 * g.TY + 6) * g.nx * sizeof(T);
     const size_t stage = (size_t)NSL * threads_x<T>(g) * sizeof(Acc<T>);
     return rows > stage ? rows : stage;
 }
