@@ -315,9 +315,10 @@ typedef struct {
     long workspace_bytes;      /* device memory owned by the problem */
     long spectrum_bytes;       /* one padded field spectrum (3 components, x-half) */
     long tensor_bytes;         /* stored tensor spectra */
-    int x_tile_rows;           /* launch shape picked by the setup autotuner: y rows per x-kernel CTA */
+    int x_tile_rows;           /* launch shape picked by the setup autotuner: y rows per x-inverse CTA */
     int yz_batch_rows;         /* ... and y rows transformed together in the y-z kernel */
     int bulk_layout;           /* 1: y-z stage in three passes (bulk grids), 0: one film kernel */
+    int x_fwd_tile_rows;       /* y rows per x-forward CTA (tuned separately) */
 } mm_info;
 MM_API int mm_problem_info(const mm_problem *prob, mm_info *info);
 

@@ -195,8 +195,8 @@ int plan(mm_problem *p)
     for (int ty = 1; ty <= 16 && ty <= next_pow2(gr.ny); ty *= 2)
         if (3 * ty * g.Gx <= 768 && mm_smem_x_for(p, ty) <= smax) p->tys[p->nty++] = ty;
     if (!p->nty) return MM_ERR_UNSUPPORTED;
-    g.TY = p->tys[p->nty - 1];
-    g.lty = ilog2i(g.TY);
+    g.TY = g.TYF = p->tys[p->nty - 1];
+    g.lty = g.ltyf = ilog2i(g.TY);
     // partial sums are sized for the smallest tile (most CTAs)
     p->nblk_x = ((gr.ny + p->tys[0] - 1) / p->tys[0]) * gr.nz;
     return MM_OK;
@@ -373,7 +373,7 @@ extern "C" int mm_setup_geometry(const mm_grid *grid, const mm_material *mat, in
         cudaFree(Nd);
         if (rc != MM_OK) break;
         if (e) { mm_set_cuda_error(e, "setup"); rc = MM_ERR_CUDA; break; }
-        if ((rc = mm_heff_configure(p, mm_smem_x_for(p, p->tys[p->nty - 1]))) != MM_OK) break;
+        if ((rc = mm_heff_configure(p)) != MM_OK) break;
         if (cudaMemsetAsync(p->mbuf[0], 0, F, s)) { rc = MM_ERR_CUDA; break; }
         {
             NvtxRange nvtx_tune("mm_autotune");
@@ -412,6 +412,7 @@ extern "C" int mm_problem_info(const mm_problem *p, mm_info *info)
     info->x_tile_rows = g.TY;
     info->yz_batch_rows = g.RB;
     info->bulk_layout = g.bulk;
+    info->x_fwd_tile_rows = g.TYF;
     return MM_OK;
 }
 

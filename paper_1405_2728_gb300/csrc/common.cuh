@@ -117,7 +117,8 @@ struct Geom {
     int Hx, C;             // Hx = Px/2 (packed complex length), C = Hx + 1 x-frequencies
     int lhx, lpy;          // log2(Hx), log2(Py)
     int Gx, Gy;            // threads per FFT row: max(1, L/8)
-    int TY;                // y rows per CTA in the x kernels
+    int TY;                // y rows per CTA of the x-inverse kernel
+    int TYF, ltyf;         // y rows per CTA of the x-forward kernel, log2
     int RB;                // y rows transformed at once in the y-z kernel (divides 3 nz)
     int rsx, rsy;          // smem row strides (complex elements) of the x and y FFT rows
     // bulk layout (grids whose padded y-z plane does not fit one CTA): the
@@ -253,7 +254,7 @@ int mm_launch_copy_result(mm_problem *p, void *dst, cudaStream_t s);
 size_t mm_smem_x_for(const mm_problem *p, int ty);
 size_t mm_smem_yz_for(const mm_problem *p);
 int mm_yz_thread_bound(const mm_problem *p);
-int mm_heff_configure(mm_problem *p, size_t sx_max);
+int mm_heff_configure(mm_problem *p);
 int mm_autotune(mm_problem *p, const int *tys, int nty, const int *rbs, int nrb, cudaStream_t s);
 int mm_launch_twiddles(mm_problem *p, cudaStream_t s);
 int mm_launch_field(mm_problem *p, const void *m, void *H, const double *hext, int mode, cudaStream_t s,

@@ -29,6 +29,7 @@
 // float pairs (TwoSum, Knuth) on the float path, and always combined across
 // CTAs in double.
 #include <cstdio>
+#include <cstring>
 
 #include "common.cuh"
 #include "fft.cuh"
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(768) k_xfwd(Geom g, FieldPtrs<T> P)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *S = reinterpret_cast<V *>(smem_raw);
     const int tid = threadIdx.x, nth = blockDim.x;
-    const int TY = g.TY, y0 = blockIdx.x * TY, z = blockIdx.y;
+    const int TY = g.TYF, y0 = blockIdx.x * TY, z = blockIdx.y;
     const int nx = g.nx, ny = g.ny, Px = g.Px;
     const long N = g.N;
     V *tw = S + 3 * TY * g.rsx;  // Px twiddles exp(-2 pi i t / Px)
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(768) k_xfwd(Geom g, FieldPtrs<T> P)
     // unpack to the real-input spectrum X[k], k = 0..Hx, and store transposed
     const int Hx = g.Hx, C = g.C;
     for (int e = tid; e < TY * 3 * C; e += nth) {
-        const int c = e % 3, rest = e / 3, yl = rest & (TY - 1), k = rest >> g.lty;
+        const int c = e % 3, rest = e / 3, yl = rest & (TY - 1), k = rest >> g.ltyf;
         const int y = y0 + yl;
         const V *row = S + (c * TY + yl) * g.rsx;
         const V Zk = row[pidx(k == Hx ? 0 : k)];
@@ -745,6 +746,12 @@ template <typename T> FieldPtrs<T> make_ptrs(mm_problem *p)
 
 static inline int round32(int n) { return (n + 31) & ~31; }
 template <typename T> int threads_x(const Geom &g) { return round32(3 * g.TY * g.Gx); }
+template <typename T> int threads_xf(const Geom &g) { return round32(3 * g.TYF * g.Gx); }
+template <typename T> size_t smem_xf_t(const Geom &g)
+{
+    typedef typename cvec<T>::type V;
+    return (size_t)3 * g.TYF * g.rsx * sizeof(V) + (size_t)g.Px * sizeof(V);
+}
 template <typename T> int threads_yz(const Geom &g) { return round32(g.RB * g.Gy); }
 
 template <typename T> size_t smem_x_t(const Geom &g)
@@ -770,9 +777,9 @@ inline int lc_of(int logL) { return MM_FFT_SPECIALISED(logL) ? logL : 0; }
 template <typename T, bool MIN>
 cudaError_t launch_xfwd(const Geom &g, const FieldPtrs<T> &P, cudaStream_t s)
 {
-    const dim3 grid((g.ny + g.TY - 1) / g.TY, g.nz);
-    const int thr = threads_x<T>(g);
-    const size_t sm = smem_x_t<T>(g);
+    const dim3 grid((g.ny + g.TYF - 1) / g.TYF, g.nz);
+    const int thr = threads_xf<T>(g);
+    const size_t sm = smem_xf_t<T>(g);
     switch (lc_of(g.lhx)) {
 #define C(L) case L: k_xfwd<T, MIN, L><<<grid, thr, sm, s>>>(g, P); break;
         MM_LC_CASES(C)
@@ -832,13 +839,13 @@ template <typename F> cudaError_t smem_attr(F *f, size_t bytes)
 }
 
 // dynamic shared memory limits of the instances this geometry launches
-template <typename T> cudaError_t configure_t(const Geom &g, size_t sx, size_t syz)
+template <typename T> cudaError_t configure_t(const Geom &g, size_t sxf, size_t sx, size_t syz)
 {
     cudaError_t e = cudaSuccess;
     switch (lc_of(g.lhx)) {
 #define C(L)                                                                                     \
     case L:                                                                                      \
-        if ((e = smem_attr(k_xfwd<T, false, L>, sx)) || (e = smem_attr(k_xfwd<T, true, L>, sx)) || \
+        if ((e = smem_attr(k_xfwd<T, false, L>, sxf)) || (e = smem_attr(k_xfwd<T, true, L>, sxf)) || \
             (e = smem_attr(k_xinv<T, MODE_HEFF, L>, sx)) || (e = smem_attr(k_xinv<T, MODE_ENERGY, L>, sx)) || \
             (e = smem_attr(k_xinv<T, MODE_MIN, L>, sx)))                                         \
             return e;                                                                            \
@@ -860,10 +867,12 @@ template <typename T> cudaError_t configure_t(const Geom &g, size_t sx, size_t s
     return cudaErrorInvalidValue;
 }
 
-// Launch-shape autotuner: time every admissible rows-per-tile TY of the x
-// kernels and rows-per-batch RB of the y-z kernel on this problem's own
-// buffers (three repetitions, best taken) and keep the fastest.  The
-// candidates are the ones mm_plan_candidates admitted.
+// Launch-shape autotuner: time every admissible rows-per-tile of the
+// x-forward kernel and, separately, of the x-inverse kernel (the two are
+// independent: the spectrum layout does not depend on the tile), and every
+// rows-per-batch RB of the y-z kernel, on this problem's own buffers (three
+// repetitions, best taken); keep the fastest of each.  The kernels run in
+// their minimiser modes on the zeroed state of a fresh problem.
 template <typename T> cudaError_t autotune_t(mm_problem *p, const int *tys, int nty, const int *rbs, int nrb,
                                              cudaStream_t s)
 {
@@ -873,29 +882,43 @@ template <typename T> cudaError_t autotune_t(mm_problem *p, const int *tys, int 
     P.H_out = (T *)p->gbuf[0];
     cudaEvent_t a, b;
     cudaError_t e;
+    // a minimiser state past its first iteration, so that the step and the
+    // step-size sums are part of what is timed (the zeroed buffers make it
+    // arithmetic on zeros and NaNs, which costs the same)
+    MinState ms;
+    memset(&ms, 0, sizeof ms);
+    ms.k = 1;
+    ms.tau = ms.tau0 = 1e-9;
+    ms.tauf = 1e-9f;
+    ms.max_iter = 1L << 40;
+    ms.status = MMS_RUNNING;
+    if ((e = cudaMemcpyAsync(p->st, &ms, sizeof ms, cudaMemcpyHostToDevice, s)) || (e = cudaStreamSynchronize(s)))
+        return e;
     if ((e = cudaEventCreate(&a))) return e;
     if ((e = cudaEventCreate(&b))) { cudaEventDestroy(a); return e; }
-    float best = 1e30f;
-    int bty = tys[0];
-    for (int i = 0; i < nty && !e; ++i) {
-        g.TY = tys[i];
-        g.lty = mm_ilog2(g.TY);
-        float tmin = 1e30f;
-        for (int r = 0; r < 3 && !e; ++r) {
-            cudaEventRecord(a, s);
-            launch_xfwd<T, false>(g, P, s);
-            launch_xinv<T, MODE_HEFF>(g, P, s, nullptr, 0, 0);
-            cudaEventRecord(b, s);
-            if ((e = cudaGetLastError()) || (e = cudaEventSynchronize(b))) break;
-            float t = 0;
-            cudaEventElapsedTime(&t, a, b);
-            if (t < tmin) tmin = t;
+    for (int which = 0; which < 2 && !e; ++which) {
+        float best = 1e30f;
+        int bty = tys[0];
+        for (int i = 0; i < nty && !e; ++i) {
+            if (which == 0) { g.TYF = tys[i]; g.ltyf = mm_ilog2(g.TYF); }
+            else { g.TY = tys[i]; g.lty = mm_ilog2(g.TY); }
+            float tmin = 1e30f;
+            for (int r = 0; r < 3 && !e; ++r) {
+                cudaEventRecord(a, s);
+                if (which == 0) launch_xfwd<T, true>(g, P, s);
+                else launch_xinv<T, MODE_MIN>(g, P, s, nullptr, 0, 0);
+                cudaEventRecord(b, s);
+                if ((e = cudaGetLastError()) || (e = cudaEventSynchronize(b))) break;
+                float t = 0;
+                cudaEventElapsedTime(&t, a, b);
+                if (t < tmin) tmin = t;
+            }
+            if (tmin < best) { best = tmin; bty = tys[i]; }
         }
-        if (tmin < best) { best = tmin; bty = tys[i]; }
+        if (which == 0) { g.TYF = bty; g.ltyf = mm_ilog2(bty); }
+        else { g.TY = bty; g.lty = mm_ilog2(bty); }
     }
-    g.TY = bty;
-    g.lty = mm_ilog2(g.TY);
-    best = 1e30f;
+    float best = 1e30f;
     int brb = rbs[0];
     for (int i = 0; i < nrb && !e && !g.bulk; ++i) {
         g.RB = rbs[i];
@@ -914,6 +937,8 @@ template <typename T> cudaError_t autotune_t(mm_problem *p, const int *tys, int 
     g.RB = brb;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
+    if (!e) e = cudaMemsetAsync(p->st, 0, sizeof(MinState), s);
+    if (!e) e = cudaMemsetAsync(p->counter, 0, 64, s);
     if (!e) p->g = g;
     return e;
 }
@@ -1007,10 +1032,15 @@ size_t mm_smem_yz_for(const mm_problem *p)
 }
 int mm_yz_thread_bound(const mm_problem *p) { return DISPATCH(p, YZBound<double>::v, YZBound<float>::v); }
 
-int mm_heff_configure(mm_problem *p, size_t sx_max)
+int mm_heff_configure(mm_problem *p)
 {
+    // limits for the largest admissible tile (shared memory grows with it)
+    Geom g = p->g;
+    g.TY = g.TYF = p->tys[p->nty - 1];
+    const size_t sx = DISPATCH(p, smem_x_t<double>(g), smem_x_t<float>(g));
+    const size_t sxf = DISPATCH(p, smem_xf_t<double>(g), smem_xf_t<float>(g));
     const size_t syz = p->g.bulk ? 0 : mm_smem_yz_for(p);
-    cudaError_t e = DISPATCH(p, configure_t<double>(p->g, sx_max, syz), configure_t<float>(p->g, sx_max, syz));
+    cudaError_t e = DISPATCH(p, configure_t<double>(g, sxf, sx, syz), configure_t<float>(g, sxf, sx, syz));
     if (!e && p->g.bulk) e = mm_bulk_configure(p);
     if (e) { mm_set_cuda_error(e, "cudaFuncSetAttribute"); return MM_ERR_CUDA; }
     return MM_OK;

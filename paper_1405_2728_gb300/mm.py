@@ -51,7 +51,8 @@ class mm_info(ctypes.Structure):
     _fields_ = [("nx", c_int), ("ny", c_int), ("nz", c_int), ("px", c_int), ("py", c_int), ("pz", c_int),
                 ("precision", c_int), ("cells", c_long), ("workspace_bytes", c_long),
                 ("spectrum_bytes", c_long), ("tensor_bytes", c_long), ("x_tile_rows", c_int),
-                ("yz_batch_rows", c_int), ("bulk_layout", c_int)]
+                ("yz_batch_rows", c_int), ("bulk_layout", c_int),
+                ("x_fwd_tile_rows", c_int)]
 
 
 class MMError(RuntimeError):
