@@ -165,8 +165,11 @@ def algorithmic_model(info, esz):
                            "flops": C * Py * (3 * (fft_flops(Pz, True, False) + fft_flops(Pz, False, True)) + Pz * 36)}
         model["y_inv"] = {"bytes": W2 + W, "flops": C * 3 * nz * fft_flops(Py, False, True)}
     else:
-        zf = 3 * (fft_flops(Pz, True, False) + fft_flops(Pz, False, False))
-        f_yz = C * (3 * nz * (fft_flops(Py, True, False) + fft_flops(Py, False, True)) + Py * (zf + Pz * 36))
+        # z direction as a direct convolution per (kx, ky): nz^2 source/target
+        # pairs of the real-even part (20 flops) and nz(nz-1) pairs of the
+        # imaginary-odd part (16 flops)
+        zc = nz * nz * 20 + nz * (nz - 1) * 16
+        f_yz = C * (3 * nz * (fft_flops(Py, True, False) + fft_flops(Py, False, True)) + Py * zc)
         model["yz_conv"] = {"bytes": 2 * W + T, "flops": f_yz}
     return model
 

@@ -59,6 +59,13 @@ namespace {
     } while (0)
 
 int next_pow2(int v) { int p = 1; while (p < v) p <<= 1; return p; }
+
+// stored tensor: film layout C * nz * 6 * (Py/2+1), bulk layout C * (Pz/2+1) * (Py/2+1) * 6
+size_t tensor_bytes(const Geom &g, size_t esz)
+{
+    return (g.bulk ? (size_t)g.C * (g.Pz / 2 + 1) * (g.Py / 2 + 1) * 6
+                   : (size_t)g.C * g.nz * 6 * (g.Py / 2 + 1)) * esz;
+}
 int ilog2i(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
 
 bool grid_ok(const mm_grid *g)
@@ -329,7 +336,7 @@ extern "C" int mm_setup_geometry(const mm_grid *grid, const mm_material *mat, in
     const size_t F = 3 * (size_t)g.N * p->esz;
     const size_t vsz = 2 * p->esz;
     const size_t Wb = (size_t)g.C * 3 * g.nz * g.ny * vsz;
-    const size_t Tb = (size_t)g.C * (g.Pz / 2 + 1) * (g.Py / 2 + 1) * 6 * p->esz;
+    const size_t Tb = tensor_bytes(g, p->esz);
     do {
         if ((rc = dalloc(p, &p->mbuf[0], F)) || (rc = dalloc(p, &p->mbuf[1], F)) ||
             (rc = dalloc(p, &p->gbuf[0], F)) || (rc = dalloc(p, &p->gbuf[1], F)) ||
@@ -408,7 +415,7 @@ extern "C" int mm_problem_info(const mm_problem *p, mm_info *info)
     info->cells = g.N;
     info->workspace_bytes = p->bytes;
     info->spectrum_bytes = (long)g.C * 3 * g.nz * g.ny * 2 * (long)p->esz;
-    info->tensor_bytes = (long)g.C * (g.Pz / 2 + 1) * (g.Py / 2 + 1) * 6 * (long)p->esz;
+    info->tensor_bytes = (long)tensor_bytes(g, p->esz);
     info->x_tile_rows = g.TY;
     info->yz_batch_rows = g.RB;
     info->bulk_layout = g.bulk;

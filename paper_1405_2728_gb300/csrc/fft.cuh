@@ -276,12 +276,3 @@ __device__ __forceinline__ void fft_row(V *row, int L, int logL, int j, const V 
 // Row lengths with compiled specialisations in the field kernels (log2 of
 // 64 .. 1024); other lengths take the generic code.
 #define MM_FFT_SPECIALISED(logL) ((logL) >= 6 && (logL) <= 10)
-
-// Small in-register DFT of length PZ (1, 2, 4 or 8) for the z direction,
-// with the same half-input / half-output pruning flags.
-template <int PZ, bool INV, bool HIN, typename V> __device__ __forceinline__ void dft_small(V *a)
-{
-    if (PZ == 2) dft2<HIN>(a[0], a[1]);
-    else if (PZ == 4) dft4<INV, HIN>(a[0], a[1], a[2], a[3]);
-    else if (PZ == 8) dft8<INV, HIN>(a);
-}

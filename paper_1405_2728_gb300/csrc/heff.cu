@@ -44,25 +44,6 @@ template <typename T, typename V> __device__ __forceinline__ T &rel(V *row, int 
     return reinterpret_cast<T *>(row + pidx(x >> 1))[x & 1];
 }
 
-// v * W^n (forward) or v * W^-n (inverse), W = exp(-2 pi i / PZ), n < PZ/2,
-// with the constants of PZ = 4 and PZ = 8 written out
-template <int PZ, bool INV, typename V> __device__ __forceinline__ V tw_pz(V v, int n)
-{
-    typedef decltype(v.x) T;
-    const T r = (T)0.70710678118654752440084436210484903928;
-    if (n == 0 || PZ <= 2) return v;
-    if (PZ == 4 || (PZ == 8 && n == 2)) return cmul_mi<INV>(v);  // W^1 of PZ = 4, W^2 of PZ = 8: -i
-    V o;
-    if (n == 1) {
-        if (INV) { o.x = r * (v.x - v.y); o.y = r * (v.x + v.y); }
-        else { o.x = r * (v.x + v.y); o.y = r * (v.y - v.x); }
-    } else {  // PZ == 8, n == 3
-        if (INV) { o.x = -r * (v.x + v.y); o.y = r * (v.x - v.y); }
-        else { o.x = r * (v.y - v.x); o.y = -r * (v.x + v.y); }
-    }
-    return o;
-}
-
 // Rows of a field [3][nz][ny][nx] copied asynchronously into shared memory:
 // dst [3][nrows][nx] receives rows y = ylo .. ylo + nrows - 1 of plane z
 // (rows outside 0..ny-1 are skipped) in 16-byte chunks (the planner checked
@@ -247,62 +228,61 @@ __global__ void __launch_bounds__(YZBound<T>::v) k_yz(Geom g, FieldPtrs<T> P)
     for (int r0 = 0; r0 < nrow; r0 += g.RB)
         fft_row<false, true, false, 1, LY>(S + (act ? r0 + rb : 0) * g.rsy, Py, g.lpy, j, tw, act);
 
-    // per ky: z transform, tensor product, inverse z transform.  The z input
-    // has nz <= PZ/2 non-zero values and only nz outputs are kept, so the
-    // PZ-point transforms split into their even and odd frequencies:
-    //   X[2k+h] = DFT_{PZ/2}(x[n] W^{nh})[k],  W = exp(-2 pi i/PZ),
-    //   y[z]    = IDFT_{PZ/2}(H_even)[z] + W^{-z} IDFT_{PZ/2}(H_odd)[z],
-    // and each half is done in turn to keep fewer values live.
-    constexpr int HZ = PZ > 1 ? PZ / 2 : 1;
-    const int hy = Py / 2, hz = PZ / 2;
-    const T *Nk = P.Nhat + (long)kx * (hz + 1) * (hy + 1) * 6;
+    // per ky: the z direction as a direct convolution (films have nz <= 4).
+    // With the tensor transformed along x and y only, K(kx, ky, dz), the
+    // field is H^_a(z) = sum_b sum_z' K_ab(z - z') m^_b(z') -- the same sums
+    // the zero-padded z-FFT, product and inverse z-FFT would form, in fewer
+    // operations and with no twiddles.  K_xx, K_yy, K_zz, K_xy are real and
+    // even in dz, K_xz and K_yz imaginary and odd in dz (and zero at dz = 0);
+    // K_xy, K_yz are odd in ky.  Stored for dz = 0 .. nz-1 as
+    // [kx][dz][component][ky <= Py/2], scaled by -Ms/(Px Py).
+    constexpr int NZM = PZ > 1 ? PZ / 2 : 1;  // nz <= NZM
+    const int hy = Py / 2, kst = hy + 1;
+    const T *Kk = P.Nhat + (long)kx * nz * 6 * kst;
     for (int ky = tid; ky < Py; ky += nth) {
         const int pky = pidx(ky);
         const int kyr = ky <= hy ? ky : Py - ky;
         const T sy = ky <= hy ? (T)1 : (T)-1;
-        V out[3][HZ];
+        V mz[3][NZM], hz[3][NZM];
 #pragma unroll
-        for (int half = 0; half < (PZ > 1 ? 2 : 1); ++half) {
-            V b[3][HZ];
+        for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
+            for (int n = 0; n < NZM; ++n) {
+                mz[c][n] = (n < nz) ? S[(c * nz + n) * g.rsy + pky] : czero<V>();
+                hz[c][n] = czero<V>();
+            }
 #pragma unroll
-                for (int n = 0; n < HZ; ++n) {
-                    const V x = (n < nz) ? S[(c * nz + n) * g.rsy + pky] : czero<V>();
-                    b[c][n] = half ? tw_pz<PZ, false>(x, n) : x;
+        for (int dz = 0; dz < NZM; ++dz) {
+            if (dz >= nz) break;
+            const T *kd = Kk + (long)dz * 6 * kst + kyr;
+            const T kxx = ldg(kd), kyy = ldg(kd + kst), kzz = ldg(kd + 2 * kst);
+            const T kxy = sy * ldg(kd + 3 * kst), kxz = ldg(kd + 4 * kst), kyz = sy * ldg(kd + 5 * kst);
+#pragma unroll
+            for (int z = 0; z < NZM; ++z)
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    // source z' = z - dz (side 0) or z + dz (side 1); K(z - z') of the
+                    // odd components is +K(dz) for z' < z and -K(dz) for z' > z
+                    if (side == 1 && dz == 0) continue;
+                    const int zp = side ? z + dz : z - dz;
+                    if (zp < 0 || zp >= NZM) continue;
+                    const V a = mz[0][zp], b = mz[1][zp], c = mz[2][zp];
+                    hz[0][z].x += kxx * a.x + kxy * b.x; hz[0][z].y += kxx * a.y + kxy * b.y;
+                    hz[1][z].x += kxy * a.x + kyy * b.x; hz[1][z].y += kxy * a.y + kyy * b.y;
+                    hz[2][z].x += kzz * c.x;             hz[2][z].y += kzz * c.y;
+                    if (dz > 0) {  // i * (+-k) * m = (-+k m.y, +-k m.x)
+                        const T sxz = side ? -kxz : kxz, syz = side ? -kyz : kyz;
+                        hz[0][z].x -= sxz * c.y;             hz[0][z].y += sxz * c.x;
+                        hz[1][z].x -= syz * c.y;             hz[1][z].y += syz * c.x;
+                        hz[2][z].x -= sxz * a.y + syz * b.y; hz[2][z].y += sxz * a.x + syz * b.x;
+                    }
                 }
-                dft_small<HZ, false, false>(b[c]);
-            }
-#pragma unroll
-            for (int kh = 0; kh < HZ; ++kh) {
-                const int kz = PZ > 1 ? 2 * kh + half : 0;
-                const int kzr = kz <= hz ? kz : PZ - kz;
-                const T sz = kz <= hz ? (T)1 : (T)-1;
-                const T *n6 = Nk + ((long)kzr * (hy + 1) + kyr) * 6;
-                const T nxx = ldg(n6 + 0), nyy = ldg(n6 + 1), nzz = ldg(n6 + 2);
-                const T nxy = sy * ldg(n6 + 3), nxz = sz * ldg(n6 + 4), nyz = sy * sz * ldg(n6 + 5);
-                const V m0 = b[0][kh], m1 = b[1][kh], m2 = b[2][kh];
-                V h0, h1, h2;
-                h0.x = nxx * m0.x + nxy * m1.x + nxz * m2.x; h0.y = nxx * m0.y + nxy * m1.y + nxz * m2.y;
-                h1.x = nxy * m0.x + nyy * m1.x + nyz * m2.x; h1.y = nxy * m0.y + nyy * m1.y + nyz * m2.y;
-                h2.x = nxz * m0.x + nyz * m1.x + nzz * m2.x; h2.y = nxz * m0.y + nyz * m1.y + nzz * m2.y;
-                b[0][kh] = h0; b[1][kh] = h1; b[2][kh] = h2;
-            }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                dft_small<HZ, true, false>(b[c]);
-#pragma unroll
-                for (int n = 0; n < HZ; ++n) {
-                    if (half == 0) out[c][n] = b[c][n];
-                    else out[c][n] = cadd(out[c][n], tw_pz<PZ, true>(b[c][n], n));
-                }
-            }
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int zz = 0; zz < HZ; ++zz)
-                if (zz < nz) S[(c * nz + zz) * g.rsy + pky] = out[c][zz];
+            for (int zz = 0; zz < NZM; ++zz)
+                if (zz < nz) S[(c * nz + zz) * g.rsy + pky] = hz[c][zz];
     }
     __syncthreads();
     for (int r0 = 0; r0 < nrow; r0 += g.RB)
