@@ -60,11 +60,11 @@ namespace {
 
 int next_pow2(int v) { int p = 1; while (p < v) p <<= 1; return p; }
 
-// stored tensor: film layout C * nz * 6 * (Py/2+1), bulk layout C * (Pz/2+1) * (Py/2+1) * 6
+// stored tensor: film layout C * max(1, Pz/2) * 6 * (Py/2+1), bulk layout C * (Pz/2+1) * (Py/2+1) * 6
 size_t tensor_bytes(const Geom &g, size_t esz)
 {
     return (g.bulk ? (size_t)g.C * (g.Pz / 2 + 1) * (g.Py / 2 + 1) * 6
-                   : (size_t)g.C * g.nz * 6 * (g.Py / 2 + 1)) * esz;
+                   : (size_t)g.C * (g.Pz > 1 ? g.Pz / 2 : 1) * 6 * (g.Py / 2 + 1)) * esz;
 }
 int ilog2i(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
 

@@ -196,7 +196,7 @@ struct FieldPtrs {
     T *gbuf[2];            // projected-gradient buffers
     V *W;                  // spectrum [C][nz][ny][3] (x-frequency slowest, component fastest)
     V *W2;                 // bulk layout only: y-transformed spectrum [C][nz][Py][3]
-    const T *Nhat;         // tensor: film [C][nz][6][Py/2+1] (x-y transform at real z offsets, scaled by
+    const T *Nhat;         // tensor: film [C][max(1,Pz/2)][6][Py/2+1] (x-y transform at real z offsets, scaled by
                            // -Ms/(Px Py)); bulk [C][Pz/2+1][Py/2+1][6] (octant of the 3-D spectrum,
                            // scaled by -Ms/(Px Py Pz))
     const V *tw_px;        // exp(-2 pi i t/Px), t < Px

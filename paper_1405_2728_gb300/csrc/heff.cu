@@ -234,11 +234,12 @@ __global__ void __launch_bounds__(YZBound<T>::v) k_yz(Geom g, FieldPtrs<T> P)
     // the zero-padded z-FFT, product and inverse z-FFT would form, in fewer
     // operations and with no twiddles.  K_xx, K_yy, K_zz, K_xy are real and
     // even in dz, K_xz and K_yz imaginary and odd in dz (and zero at dz = 0);
-    // K_xy, K_yz are odd in ky.  Stored for dz = 0 .. nz-1 as
+    // K_xy, K_yz are odd in ky.  Stored for dz = 0 .. NZM-1 (zero beyond
+    // nz - 1, so that every load is unconditional) as
     // [kx][dz][component][ky <= Py/2], scaled by -Ms/(Px Py).
     constexpr int NZM = PZ > 1 ? PZ / 2 : 1;  // nz <= NZM
     const int hy = Py / 2, kst = hy + 1;
-    const T *Kk = P.Nhat + (long)kx * nz * 6 * kst;
+    const T *Kk = P.Nhat + (long)kx * NZM * 6 * kst;
     for (int ky = tid; ky < Py; ky += nth) {
         const int pky = pidx(ky);
         const int kyr = ky <= hy ? ky : Py - ky;
@@ -253,7 +254,6 @@ __global__ void __launch_bounds__(YZBound<T>::v) k_yz(Geom g, FieldPtrs<T> P)
             }
 #pragma unroll
         for (int dz = 0; dz < NZM; ++dz) {
-            if (dz >= nz) break;
             const T *kd = Kk + (long)dz * 6 * kst + kyr;
             const T kxx = ldg(kd), kyy = ldg(kd + kst), kzz = ldg(kd + 2 * kst);
             const T kxy = sy * ldg(kd + 3 * kst), kxz = ldg(kd + 4 * kst), kyz = sy * ldg(kd + 5 * kst);

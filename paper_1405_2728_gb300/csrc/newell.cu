@@ -146,20 +146,24 @@ __global__ void k_extract(int c, int Px, int Py, int Pz, const double2 *F, doubl
 }
 
 // Film layout: the tensor transformed along x and y only, at real z offsets
-// dz = 0 .. nz-1, for the direct z-convolution of the film kernel:
-// K[kx][dz][c][ky], kx <= Px/2, ky <= Py/2, scaled by -Ms/(Px Py).  The xx,
-// yy, zz and xy transforms are real, the xz and yz transforms imaginary (odd
-// in x or y and in z); their imaginary parts are stored, and zero at dz = 0.
+// dz = 0 .. nzf-1 with nzf = max(1, Pz/2) (zero for dz >= nz), for the
+// direct z-convolution of the film kernel: K[kx][dz][c][ky], kx <= Px/2,
+// ky <= Py/2, scaled by -Ms/(Px Py).  The xx, yy, zz and xy transforms are
+// real, the xz and yz transforms imaginary (odd in x or y and in z); their
+// imaginary parts are stored, and zero at dz = 0.
 template <typename T>
-__global__ void k_extract_film(int c, int Px, int Py, int nz, const double2 *F, double scale, T *K)
+__global__ void k_extract_film(int c, int Px, int Py, int nz, int nzf, const double2 *F, double scale, T *K)
 {
     const int hx = Px / 2, hy = Py / 2;
-    const long tot = (long)(hx + 1) * nz * (hy + 1);
+    const long tot = (long)(hx + 1) * nzf * (hy + 1);
     for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < tot; p += (long)gridDim.x * blockDim.x) {
-        const long ky = p % (hy + 1), dz = (p / (hy + 1)) % nz, kx = p / ((long)(hy + 1) * nz);
-        const double2 f = F[(dz * Py + ky) * Px + kx];
-        const double v = c < 4 ? f.x : (dz == 0 ? 0.0 : f.y);
-        K[((kx * nz + dz) * 6 + c) * (hy + 1) + ky] = (T)(scale * v);
+        const long ky = p % (hy + 1), dz = (p / (hy + 1)) % nzf, kx = p / ((long)(hy + 1) * nzf);
+        double v = 0.0;
+        if (dz < nz) {
+            const double2 f = F[(dz * Py + ky) * Px + kx];
+            v = c < 4 ? f.x : (dz == 0 ? 0.0 : f.y);
+        }
+        K[((kx * nzf + dz) * 6 + c) * (hy + 1) + ky] = (T)(scale * v);
     }
 }
 
@@ -194,7 +198,8 @@ int mm_newell_device(const mm_grid *gr, double *N_dev, cudaStream_t s)
 
 // Tensor spectra into p->Nhat in the precision of p: bulk layout
 // [Px/2+1][Pz/2+1][Py/2+1][6] (3-D transform, octant); film layout
-// [Px/2+1][nz][6][Py/2+1] (x-y transform at real z offsets, k_extract_film).
+// [Px/2+1][max(1, Pz/2)][6][Py/2+1] (x-y transform at real z offsets,
+// k_extract_film).
 int mm_tensor_spectrum(mm_problem *p, const double *N_dev, cudaStream_t s)
 {
     const Geom &g = p->g;
@@ -223,7 +228,8 @@ int mm_tensor_spectrum(mm_problem *p, const double *N_dev, cudaStream_t s)
     if (eblocks > 152 * 32) eblocks = 152 * 32;
     // film layout: transforms along x and y only (the film kernel convolves z directly)
     const int naxes = g.bulk ? 3 : 2;
-    const long fext = (long)(g.Px / 2 + 1) * g.nz * (g.Py / 2 + 1);
+    const int nzf = g.Pz > 1 ? g.Pz / 2 : 1;
+    const long fext = (long)(g.Px / 2 + 1) * nzf * (g.Py / 2 + 1);
     long fblocks = (fext + 255) / 256;
     if (fblocks > 152 * 32) fblocks = 152 * 32;
     for (int c = 0; c < 6 && !e; ++c) {
@@ -240,9 +246,9 @@ int mm_tensor_spectrum(mm_problem *p, const double *N_dev, cudaStream_t s)
         if (!g.bulk) {
             const double fscale = -g.Ms / ((double)g.Px * g.Py);
             if (p->precision == MM_FP64)
-                k_extract_film<double><<<(int)fblocks, 256, 0, s>>>(c, g.Px, g.Py, g.nz, F, fscale, (double *)p->Nhat);
+                k_extract_film<double><<<(int)fblocks, 256, 0, s>>>(c, g.Px, g.Py, g.nz, nzf, F, fscale, (double *)p->Nhat);
             else
-                k_extract_film<float><<<(int)fblocks, 256, 0, s>>>(c, g.Px, g.Py, g.nz, F, fscale, (float *)p->Nhat);
+                k_extract_film<float><<<(int)fblocks, 256, 0, s>>>(c, g.Px, g.Py, g.nz, nzf, F, fscale, (float *)p->Nhat);
         } else if (p->precision == MM_FP64) {
             k_extract<double><<<(int)eblocks, 256, 0, s>>>(c, g.Px, g.Py, g.Pz, F, scale, (double *)p->Nhat);
         } else {
