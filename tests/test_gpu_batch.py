@@ -54,3 +54,25 @@ def test_batch_equals_single_sweeps_and_oracle(mmlib):
         assert abs(a["H_sw"] - b["H_sw"]) <= step * (1 + 1e-9)
     assert abs(a["M_r"] - b["M_r"]) <= 1e-3
     batch.close()
+
+
+def test_batch_fp32_mixed_with_fp64(mmlib):
+    # a batch may mix precisions; each member equals its own single sweep
+    films = small_films()[:3]
+    precs = [mmlib.MM_FP32, mmlib.MM_FP64, mmlib.MM_FP32]
+    probs = [mmlib.mm_setup_geometry(mmlib.make_grid(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz),
+                                     mmlib.make_material(w.Ms, w.A, w.K), pr) for w, pr in zip(films, precs)]
+    dts = [torch.float32 if pr == mmlib.MM_FP32 else torch.float64 for pr in precs]
+    F = films[0].fields()[:5]
+    opts = mmlib.make_opts(tol=1e-5)
+    batch = mmlib.mm_batch_create(probs)
+    ms = [dev(w.initial_m(), dt) for w, dt in zip(films, dts)]
+    st, mavg, res = mmlib.mm_batch_sweep(batch, ms, F, opts=opts)
+    assert st == mmlib.MM_OK
+    for i, (w, p, dt) in enumerate(zip(films, probs, dts)):
+        m1 = dev(w.initial_m(), dt)
+        st1, mavg1, _ = mmlib.mm_hysteresis_sweep(p, m1, F, opts=opts)
+        assert st1 == mmlib.MM_OK
+        assert np.array_equal(mavg[i], mavg1), i
+        assert torch.equal(ms[i], m1), i
+    batch.close()

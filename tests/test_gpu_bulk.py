@@ -154,3 +154,35 @@ def test_cube_256_full_size(mmlib):
     err = float(torch.linalg.vector_norm(H32 - H64) / torch.linalg.vector_norm(H64))
     assert err <= 1e-5, err
     assert np.max(np.abs(E32 - E64)) <= 1e-5 * np.max(np.abs(E64)), (E32, E64)
+
+
+def test_bulk_energy_gradient_and_hessian_vec(mmlib):
+    # the differentiation calls run the same field chain, so they hold in the bulk layout too
+    w, prob, oprob = small_cube(mmlib, 10, 6)
+    assert _info(mmlib, prob)["bulk_layout"] == 1
+    m = inputs.random_unit_m(oprob.shape, 91)
+    Hext = (4e5, 1e5, -2e5)
+    d = om.Demag(oprob)
+    H = om.heff(oprob, m, Hext, d)
+    G = torch.empty((3,) + oprob.shape, dtype=torch.float64, device="cuda")
+    mmlib.mm_energy_gradient(prob, dev(m), Hext, G)
+    assert rel_l2(G.cpu().numpy(), -om.MU0 * oprob.Ms * oprob.V * H) <= 1e-10
+    v = om.project(m, inputs.random_unit_m(oprob.shape, 92))
+    Av = torch.empty((3,) + oprob.shape, dtype=torch.float64, device="cuda")
+    mmlib.mm_hessian_vec(prob, dev(m), Hext, dev(v), Av)
+    assert rel_l2(Av.cpu().numpy(), om.hessian_vec(oprob, m, H, v, d)) <= 1e-10
+
+
+def test_bulk_fp32_fixed_steps_follow_fp64(mmlib):
+    # FP32 minimiser steps on a granular cube track the FP64 run (same start, 20 steps)
+    w, p64, oprob = small_cube(mmlib, 12, 8)
+    _, p32, _ = small_cube(mmlib, 12, 8, precision=mmlib.MM_FP32)
+    m0 = inputs.random_unit_m(oprob.shape, 12)
+    H = w.fields()[30]
+    m64, m32 = dev(m0), dev(m0, torch.float32)
+    opts = mmlib.make_opts(tol=0.0, max_iter=20)
+    _, r64 = mmlib.mm_minimize(p64, m64, H, opts)
+    _, r32 = mmlib.mm_minimize(p32, m32, H, opts)
+    assert r64.iters == r32.iters == 20
+    assert rel_l2(m32.double().cpu().numpy(), m64.cpu().numpy()) <= 1e-3
+    assert np.max(np.abs(torch.linalg.vector_norm(m32.double(), dim=0).cpu().numpy() - 1)) < 2e-6
