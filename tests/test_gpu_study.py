@@ -1,0 +1,35 @@
+"""SP1 convergence study (Section 4) through the library, on the 10 nm grid:
+the loops converge at every field value, the metrics are well defined, and
+halving the field step moves the coercive field by less than the coarse
+step (the paper's statement that 0.5 mT steps do not change the loop)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1405_2728_gb300 import inputs, study
+
+pytestmark = pytest.mark.gpu
+
+
+def test_direction_and_sweep():
+    h = study.direction("short")
+    assert abs(np.linalg.norm(h) - 1) < 1e-15 and abs(math.degrees(math.atan2(h[0], h[1])) - 1.0) < 1e-12
+    H = study.sweep_fields(study.direction("long"), 50.0, 0.5)
+    assert H.shape == (401, 3)
+    b = H @ study.direction("long") * inputs.MU0 * 1e3
+    assert abs(b[0] - 50) < 1e-9 and abs(b[200] + 50) < 1e-9 and abs(b[-1] - 50) < 1e-9
+
+
+def test_sp1_10nm_step_halving(mmlib):
+    out = {}
+    for step in (1.0, 0.5):
+        met, rem, evals, sec = study.run_loop(10.0, step, "long", mmlib.MM_FP64)
+        assert met["converged"] and met["grid"] == [200, 100, 2]
+        assert met["H_sw"] is not None and met["M_r"] is not None
+        hc = met["H_c"] * inputs.MU0 * 1e3
+        assert -50.0 < hc < 0.0
+        assert abs(met["M_r"][0]) <= 1.0
+        assert np.allclose(np.linalg.norm(rem, axis=0), 1.0, atol=1e-12)
+        out[step] = hc
+    assert abs(out[1.0] - out[0.5]) <= 1.0, out
