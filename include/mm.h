@@ -314,7 +314,7 @@ typedef struct {
     long cells;
     long workspace_bytes;      /* device memory owned by the problem */
     long spectrum_bytes;       /* one padded field spectrum (3 components, x-half) */
-    long tensor_bytes;         /* stored tensor spectra */
+    long tensor_bytes;         /* stored demagnetisation tensor (transformed; layout depends on bulk_layout) */
     int x_tile_rows;           /* launch shape picked by the setup autotuner: y rows per x-inverse CTA */
     int yz_batch_rows;         /* ... and y rows transformed together in the y-z kernel */
     int bulk_layout;           /* 1: y-z stage in three passes (bulk grids), 0: one film kernel */

@@ -1,20 +1,21 @@
 // Effective-field and minimiser-step kernels (sm_103a).
 //
 // One evaluation of H_eff (Eq. effective_field; Sections 3 and 4) is three
-// kernels over the zero-padded grid; in the minimiser (Section 2) the last of
+// kernels over the zero-padded grid for films (bulk grids replace k_yz by
+// the three passes of bulk.cu); in the minimiser (Section 2) the last of
 // them also finishes the iteration:
 //
-//  k_xfwd     per (z, tile of TY rows): optional minimiser step (the closed
+//  k_xfwd     per (z, tile of TYF rows): optional minimiser step (the closed
 //             form of the midpoint scheme, Eq. implicit_gradient_descent, or
 //             the renormalised explicit step) fused with the real-to-complex
 //             FFT along x of the three components, zero padding nx -> Px,
 //             written transposed to the spectrum W[kx][z][y][c].
 //  k_yz       per x-frequency kx: FFT along y (padding ny -> Py) in shared
-//             memory, then per ky in registers FFT along z, the product with
-//             the symmetric 3x3 tensor spectrum (H^ = -Ms N^ m^, normalisation
-//             folded into N^), inverse FFT along z, inverse FFT along y keeping
-//             the first ny rows.
-//  k_xinv     per (z, tile): complex-to-real inverse FFT along x keeping nx
+//             memory; then per ky, in registers, the z direction as a direct
+//             convolution with the tensor transformed along x and y
+//             (H^ = -Ms N m^, nz <= 4, normalisation folded into the tensor);
+//             then the inverse FFT along y keeping the first ny rows.
+//  k_xinv     per (z, tile of TY rows): complex-to-real inverse FFT along x keeping nx
 //             values, then the local terms: exchange (six-point stencil, free
 //             faces), uniaxial anisotropy, Zeeman.  Depending on the mode it
 //             writes H, or accumulates the energy terms, or forms the projected

@@ -70,3 +70,24 @@ def test_granular_cube_inputs():
     assert abs(b[0]) < 1e-15 and abs(b[160] - 8.0) < 1e-12 and abs(b[-1] + 8.0) < 1e-12
     assert np.all(np.diff(b[:161]) > 0) and np.all(np.diff(b[160:]) < 0)
     assert np.all(H[:, 1:] == 0)
+
+
+def test_study_directions_and_sweep():
+    # SP1 field directions (1 degree off each edge) and the +50 -> -50 -> +50 mT sweep
+    from paper_1405_2728_gb300 import study
+    h = study.direction("short")
+    assert abs(np.linalg.norm(h) - 1) < 1e-15 and abs(math.degrees(math.atan2(h[0], h[1])) - 1.0) < 1e-12
+    h = study.direction("long")
+    assert abs(math.degrees(math.atan2(h[1], h[0])) - 1.0) < 1e-12
+    H = study.sweep_fields(h, 50.0, 0.5)
+    assert H.shape == (401, 3)
+    b = H @ h * inputs.MU0 * 1e3
+    assert abs(b[0] - 50) < 1e-9 and abs(b[200] + 50) < 1e-9 and abs(b[-1] - 50) < 1e-9
+    # loop metrics of a hand-made loop: <m>.h = tanh((H - Hc) / w) on the way down
+    hh = b * 1e-3 / inputs.MU0
+    p = np.tanh((b + 7.25) / 2.0)
+    mavg = np.outer(p, h)
+    met = study.loop_metrics(H, mavg, h)
+    assert met["H_sw"] * inputs.MU0 * 1e3 == -7.5
+    assert -7.5 < met["H_c"] * inputs.MU0 * 1e3 < -7.0
+    assert abs(met["M_r"][0] - np.tanh(7.25 / 2.0) * h[0]) < 1e-12

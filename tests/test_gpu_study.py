@@ -2,23 +2,12 @@
 the loops converge at every field value, the metrics are well defined, and
 halving the field step moves the coercive field by less than the coarse
 step (the paper's statement that 0.5 mT steps do not change the loop)."""
-import math
-
 import numpy as np
 import pytest
 
 from paper_1405_2728_gb300 import inputs, study
 
 pytestmark = pytest.mark.gpu
-
-
-def test_direction_and_sweep():
-    h = study.direction("short")
-    assert abs(np.linalg.norm(h) - 1) < 1e-15 and abs(math.degrees(math.atan2(h[0], h[1])) - 1.0) < 1e-12
-    H = study.sweep_fields(study.direction("long"), 50.0, 0.5)
-    assert H.shape == (401, 3)
-    b = H @ study.direction("long") * inputs.MU0 * 1e3
-    assert abs(b[0] - 50) < 1e-9 and abs(b[200] + 50) < 1e-9 and abs(b[-1] - 50) < 1e-9
 
 
 def test_sp1_10nm_step_halving(mmlib):
