@@ -175,14 +175,19 @@ def algorithmic_model(info, esz):
 
 
 def kernel_source_hash():
-    """sha256 (first 16 hex) of the CUDA sources, to tell whether a committed
-    ncu summary still describes the kernels that run."""
+    """sha256 (first 16 hex) of the CUDA sources with comments and whitespace
+    removed, to tell whether a committed ncu summary still describes the
+    kernels that run (an edit of a comment does not change them)."""
     import glob
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in sorted(glob.glob(os.path.join(ROOT, "paper_1405_2728_gb300", "csrc", "*"))):
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)  # block comments
+        text = re.sub(r"//[^\n]*", " ", text)               # line comments
+        h.update(re.sub(r"\s+", "", text).encode())
     return h.hexdigest()[:16]
 
 
