@@ -174,15 +174,19 @@ def algorithmic_model(info, esz):
     return model
 
 
+KERNEL_SOURCES = ("common.cuh", "fft.cuh", "heff.cu")  # what the three film field kernels compile from
+
+
 def kernel_source_hash():
-    """sha256 (first 16 hex) of the CUDA sources with comments and whitespace
-    removed, to tell whether a committed ncu summary still describes the
-    kernels that run (an edit of a comment does not change them)."""
-    import glob
+    """sha256 (first 16 hex) of the sources of the film field kernels with
+    comments and whitespace removed, to tell whether a committed ncu summary
+    still describes the kernels that run (an edit of a comment, or of host
+    code elsewhere, does not change them)."""
     import hashlib
     import re
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1405_2728_gb300", "csrc", "*"))):
+    for name in KERNEL_SOURCES:
+        f = os.path.join(ROOT, "paper_1405_2728_gb300", "csrc", name)
         with open(f, encoding="utf-8") as fh:
             text = fh.read()
         text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)  # block comments

@@ -108,32 +108,41 @@ extern "C" MM_API int mm_batch_sweep(mm_batch *b, void *const *m_list, const dou
     cudaError_t e = cudaEventRecord(b->start_ev, s);
     for (size_t i = 0; i < P && !e; ++i) e = cudaStreamWaitEvent(b->streams[i], b->start_ev, 0);
     if (e) { mm_set_cuda_error(e, "mm_batch_sweep"); return MM_ERR_CUDA; }
-    for (size_t i = 0; i < P; ++i) {
+    // issue everything; on a failure stop issuing, but still join every
+    // problem stream to the caller's stream so that no work is left unordered
+    rc = MM_OK;
+    for (size_t i = 0; i < P && rc == MM_OK; ++i) {
         mm_problem *p = b->probs[i];
         const size_t F = 3 * (size_t)p->g.N * p->esz;
-        if ((rc = mm_copy_user(p->mbuf[0], m_list[i], F, true, mm_is_device_ptr(m_list[i]), b->streams[i]))) return rc;
+        rc = mm_copy_user(p->mbuf[0], m_list[i], F, true, mm_is_device_ptr(m_list[i]), b->streams[i]);
     }
-    for (int j = start; j < n; ++j)
-        for (size_t i = 0; i < P; ++i) {
+    for (int j = start; j < n && rc == MM_OK; ++j)
+        for (size_t i = 0; i < P && rc == MM_OK; ++i) {
             mm_problem *p = b->probs[i];
             cudaStream_t si = b->streams[i];
-            if ((rc = mm_launch_init_state(p, H_list + 3 * j, opts, j == start, si))) return rc;
+            if ((rc = mm_launch_init_state(p, H_list + 3 * j, opts, j == start, si))) break;
             e = cudaGraphLaunch(p->gexec, si);
-            if (e) { mm_set_cuda_error(e, "cudaGraphLaunch(batch)"); return MM_ERR_CUDA; }
-            if ((rc = mm_launch_record(p, j, si))) return rc;
+            if (e) { mm_set_cuda_error(e, "cudaGraphLaunch(batch)"); rc = MM_ERR_CUDA; break; }
+            rc = mm_launch_record(p, j, si);
         }
-    for (size_t i = 0; i < P; ++i) {
+    for (size_t i = 0; i < P && rc == MM_OK; ++i) {
         mm_problem *p = b->probs[i];
         cudaStream_t si = b->streams[i];
         const size_t F = 3 * (size_t)p->g.N * p->esz;
         const bool mdev = mm_is_device_ptr(m_list[i]);
-        if ((rc = mm_launch_copy_result(p, mdev ? m_list[i] : p->stage_out, si))) return rc;
-        if (!mdev && (rc = mm_copy_user(m_list[i], p->stage_out, F, false, true, si))) return rc;
-        // join: the caller's stream waits for every problem stream
-        if ((e = cudaEventRecord(b->done[i], si)) || (e = cudaStreamWaitEvent(s, b->done[i], 0))) {
+        if ((rc = mm_launch_copy_result(p, mdev ? m_list[i] : p->stage_out, si))) break;
+        if (!mdev) rc = mm_copy_user(m_list[i], p->stage_out, F, false, true, si);
+    }
+    // join: the caller's stream waits for every problem stream
+    for (size_t i = 0; i < P; ++i) {
+        if ((e = cudaEventRecord(b->done[i], b->streams[i])) || (e = cudaStreamWaitEvent(s, b->done[i], 0))) {
             mm_set_cuda_error(e, "mm_batch_sweep");
-            return MM_ERR_CUDA;
+            if (rc == MM_OK) rc = MM_ERR_CUDA;
         }
+    }
+    if (rc != MM_OK) {
+        cudaStreamSynchronize(s);
+        return rc;
     }
     std::vector<StepRecord> rec((size_t)n);
     int first_bad = MM_OK;
