@@ -34,13 +34,27 @@ __global__ void __launch_bounds__(BulkBound<T>::v) k_ypass(Geom g, FieldPtrs<T> 
     const int kx = blockIdx.x, z0 = blockIdx.y * ZB;
     const int zb = min(ZB, nz - z0);
     V *tw = S + 3 * ZB * rs;
-    load_twiddles(tw, P.tw_py, Py);
+    load_twiddles_async(tw, P.tw_py, Py);
     const long first = (long)kx * nz + z0;  // first (kx, z) row pair of this CTA
     const int lin = INV ? Py : ny;           // input length per (z, c) row
     const V *src = INV ? P.W2 + first * Py * 3 : P.W + first * ny * 3;
-    for (int e = tid; e < zb * lin * 3; e += nth) {  // [zl][y][c] -> row (c, zl)
-        const int c = e % 3, rest = e / 3, zl = rest / lin, y = rest - zl * lin;
-        S[(c * ZB + zl) * rs + pidx(y)] = src[e];
+    // [zl][y][c] -> row (c, zl); PF loads per thread in flight before use
+    constexpr int PF = sizeof(T) == 4 ? 8 : 4;
+    const int tot = zb * lin * 3;
+    for (int e0 = tid; e0 < tot; e0 += PF * nth) {
+        V v[PF];
+#pragma unroll
+        for (int i = 0; i < PF; ++i) {
+            const int e = e0 + i * nth;
+            if (e < tot) v[i] = __ldcg(src + e);
+        }
+#pragma unroll
+        for (int i = 0; i < PF; ++i) {
+            const int e = e0 + i * nth;
+            if (e >= tot) break;
+            const int c = e % 3, rest = e / 3, zl = rest / lin, y = rest - zl * lin;
+            S[(c * ZB + zl) * rs + pidx(y)] = v[i];
+        }
     }
     if (!INV) {
         const int npad = Py - ny;
@@ -50,6 +64,7 @@ __global__ void __launch_bounds__(BulkBound<T>::v) k_ypass(Geom g, FieldPtrs<T> 
             S[(c * ZB + zl) * rs + pidx(y)] = czero<V>();
         }
     }
+    cp_async_wait_all();
     __syncthreads();
     const int Gy = g.Gy, RB = g.RBY;
     const int rb = tid / Gy, j = tid - rb * Gy;
@@ -78,13 +93,30 @@ __global__ void __launch_bounds__(BulkBound<T>::v) k_zconv(Geom g, FieldPtrs<T> 
     const int kx = blockIdx.x, ky0 = blockIdx.y * KB;
     const int kb = min(KB, Py - ky0);
     V *tw = S + 3 * KB * rs;
-    load_twiddles(tw, P.tw_pz, Pz);
-    // W2[kx][z][ky0 + kyl][c], z < nz -> row (c, kyl), element z
+    load_twiddles_async(tw, P.tw_pz, Pz);
+    // W2[kx][z][ky0 + kyl][c], z < nz -> row (c, kyl), element z; PF loads
+    // per thread in flight before use
     V *base = P.W2 + ((long)kx * nz * Py + ky0) * 3;
     const long zs = (long)Py * 3;
-    for (int e = tid; e < nz * kb * 3; e += nth) {
-        const int c = e % 3, rest = e / 3, kyl = rest % kb, z = rest / kb;
-        S[(c * KB + kyl) * rs + pidx(z)] = base[(long)z * zs + kyl * 3 + c];
+    constexpr int PF = sizeof(T) == 4 ? 8 : 4;
+    const int tot = nz * kb * 3;
+    for (int e0 = tid; e0 < tot; e0 += PF * nth) {
+        V v[PF];
+#pragma unroll
+        for (int i = 0; i < PF; ++i) {
+            const int e = e0 + i * nth;
+            if (e < tot) {
+                const int c = e % 3, rest = e / 3, kyl = rest % kb, z = rest / kb;
+                v[i] = __ldcg(base + (long)z * zs + kyl * 3 + c);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < PF; ++i) {
+            const int e = e0 + i * nth;
+            if (e >= tot) break;
+            const int c = e % 3, rest = e / 3, kyl = rest % kb, z = rest / kb;
+            S[(c * KB + kyl) * rs + pidx(z)] = v[i];
+        }
     }
     const int npad = Pz - nz;
     for (int e = tid; e < 3 * kb * npad; e += nth) {
@@ -92,6 +124,7 @@ __global__ void __launch_bounds__(BulkBound<T>::v) k_zconv(Geom g, FieldPtrs<T> 
         const int c = r / kb, kyl = r - c * kb;
         S[(c * KB + kyl) * rs + pidx(z)] = czero<V>();
     }
+    cp_async_wait_all();
     __syncthreads();
     const int Gz = g.Gz, RB = g.RBZ;
     const int rb = tid / Gz, j = tid - rb * Gz;
