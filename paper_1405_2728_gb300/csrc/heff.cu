@@ -196,8 +196,16 @@ __global__ void __launch_bounds__(YZBound<T>::v) k_yz(Geom g, FieldPtrs<T> P)
     const int ny = g.ny, nz = g.nz, Py = g.Py;
     const int nrow = 3 * nz;
     V *Wk = P.W + (long)kx * nrow * ny;
-    V *tw = S + nrow * g.rsy;  // Py twiddles
-    load_twiddles_async(tw, P.tw_py, Py);
+    // Py twiddles: a shared copy in float; the double kernel reads them from
+    // global memory (L1), which keeps its shared memory within two CTAs per SM
+    const V *tw;
+    if constexpr (sizeof(T) == 4) {
+        V *tws = S + nrow * g.rsy;
+        load_twiddles_async(tws, P.tw_py, Py);
+        tw = tws;
+    } else {
+        tw = P.tw_py;
+    }
 
     // Wk[z][y][c] -> row (c, z); PF loads per thread in flight before use
     constexpr int PF = sizeof(T) == 4 ? 8 : 4;
@@ -746,7 +754,8 @@ template <typename T> size_t smem_x_t(const Geom &g)
 template <typename T> size_t smem_yz_t(const Geom &g)
 {
     typedef typename cvec<T>::type V;
-    return (size_t)3 * g.nz * g.rsy * sizeof(V) + (size_t)g.Py * sizeof(V);
+    // the float kernel also holds the Py twiddles (the double kernel reads them from global memory)
+    return (size_t)3 * g.nz * g.rsy * sizeof(V) + (sizeof(T) == 4 ? (size_t)g.Py * sizeof(V) : 0);
 }
 
 // The field kernels are compiled for FFT row lengths 2^6 .. 2^10 (template
