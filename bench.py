@@ -283,6 +283,100 @@ def cufft_demag_ms(info, tdt, dev, reps=20):
     return a.elapsed_time(b) / reps
 
 
+def run_full_loop(args, w, prob, m, F, opts, stream, tdt, esz, info, dev):
+    """One whole hysteresis loop: every field value of the workload's sweep in
+    one mm_hysteresis_sweep call from the seeded start, timed with CUDA
+    events (after W untimed field values on the same problem as warm-up)."""
+    import torch
+    from paper_1405_2728_gb300 import inputs, mm
+    m_init = m.clone()
+    mm.mm_hysteresis_sweep(prob, m, F[: args.warmup], opts=opts, stream=stream)   # warm-up
+    m.copy_(m_init)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(int(str(dev).split(":")[-1] or 0))
+    with sampler:
+        torch.cuda.synchronize()
+        a.record(stream)
+        st, mavg, res = mm.mm_hysteresis_sweep(prob, m, F, opts=opts, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+    sec = a.elapsed_time(b) / 1e3
+    evals = sum(r.heff_evals for r in res)
+    hhat = F[int(np.argmax(np.linalg.norm(F, axis=1)))]
+    hhat = hhat / np.linalg.norm(hhat)
+    line = {"metric": METRIC, "value": evals / sec, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if esz == 8 else "f32", "data": "synthetic",
+            "config": {"workload": w.name, "cells": [w.nx, w.ny, w.nz], "precision": args.precision,
+                       "step": f"one whole loop: {len(F)} field values minimised to tol {w.tol:g}"},
+            "loop_time_s": sec, "loop_evals": int(evals),
+            "converged_field_values": int(sum(r.converged for r in res)), "field_values": len(F),
+            "status": int(st), "gpu_launches": int(sum(r.kernel_launches for r in res)),
+            "clocks": sampler.summary()}
+    h = (F @ hhat) * inputs.MU0 * 1e3
+    p = mavg @ hhat
+    nd = 1
+    while nd < len(h) and h[nd] < h[nd - 1]:
+        nd += 1
+    sw = [float(h[i]) for i in range(1, nd) if p[i] < 0]
+    line["H_sw_mT"] = sw[0] if sw else None
+    print(json.dumps(line))
+    prob.close()
+    return 0
+
+
+def run_mixed_loop(args, w, dev):
+    """One whole loop with mm_hysteresis_sweep_mixed: per field value FP32 to
+    --mixed-tol, then FP64 to the workload's tolerance; timed with CUDA events."""
+    import torch
+    from paper_1405_2728_gb300 import inputs, mm
+    grid = mm.make_grid(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz)
+    mat = mm.make_material(w.Ms, w.A, w.K, K_cell=w.K_cell, u_cell=w.u_cell)
+    lo = mm.mm_setup_geometry(grid, mat, mm.MM_FP32)
+    hi = mm.mm_setup_geometry(grid, mat, mm.MM_FP64)
+    F = w.fields()
+    o_lo = mm.make_opts(tol=args.mixed_tol, max_iter=20000)
+    o_hi = mm.make_opts(tol=w.tol, max_iter=args.max_iter)
+    stream = torch.cuda.current_stream(dev)
+    m0 = torch.from_numpy(w.initial_m()).to(device=dev, dtype=torch.float64).contiguous()
+    m = m0.clone()
+    mm.mm_hysteresis_sweep_mixed(lo, hi, m, F[: args.warmup], opts_lo=o_lo, opts_hi=o_hi, stream=stream)
+    m.copy_(m0)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(int(str(dev).split(":")[-1] or 0))
+    with sampler:
+        torch.cuda.synchronize()
+        a.record(stream)
+        st, mavg, rl, rh = mm.mm_hysteresis_sweep_mixed(lo, hi, m, F, opts_lo=o_lo, opts_hi=o_hi, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+    sec = a.elapsed_time(b) / 1e3
+    ev_lo, ev_hi = sum(r.heff_evals for r in rl), sum(r.heff_evals for r in rh)
+    hhat = F[int(np.argmax(np.linalg.norm(F, axis=1)))]
+    hhat = hhat / np.linalg.norm(hhat)
+    h = (F @ hhat) * inputs.MU0 * 1e3
+    p = mavg @ hhat
+    nd = 1
+    while nd < len(h) and h[nd] < h[nd - 1]:
+        nd += 1
+    sw = [float(h[i]) for i in range(1, nd) if p[i] < 0]
+    line = {"metric": METRIC, "value": (ev_lo + ev_hi) / sec, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": w.name, "cells": [w.nx, w.ny, w.nz], "precision": "mixed",
+                       "step": f"one whole loop: {len(F)} field values, FP32 to tol {args.mixed_tol:g} "
+                               f"then FP64 to tol {w.tol:g}"},
+            "loop_time_s": sec, "loop_evals_fp32": int(ev_lo), "loop_evals_fp64": int(ev_hi),
+            "converged_field_values": int(sum(r.converged for r in rh)), "field_values": len(F),
+            "status": int(st), "H_sw_mT": sw[0] if sw else None,
+            "gpu_launches": int(sum(r.kernel_launches for r in rl) + sum(r.kernel_launches for r in rh)),
+            "clocks": sampler.summary()}
+    print(json.dumps(line))
+    lo.close()
+    hi.close()
+    return 0
+
+
 def all_workloads(inputs):
     return {**inputs.WORKLOADS, **inputs.BULK_WORKLOADS}
 
@@ -412,9 +506,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed"],
+                    help="mixed: FP32 minimisation to --mixed-tol, then FP64 to the final tolerance (with --full-loop)")
+    ap.add_argument("--mixed-tol", type=float, default=3e-5)
     ap.add_argument("--workload", default="film_512x256x4")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--full-loop", action="store_true",
+                    help="time one whole hysteresis loop (every field value, one sweep call) instead of K steps")
     ap.add_argument("--max-iter", type=int, default=200000,
                     help="iteration cap per field value (a bounded step for very slow workloads)")
     ap.add_argument("--profile-stages", type=int, default=0,
@@ -441,6 +539,10 @@ def main():
     if args.workload == "batch64":
         return run_batch(args, ws, rank, local, dev)
     w = all_workloads(inputs)[args.workload]()
+    if args.precision == "mixed":
+        if not args.full_loop:
+            ap.error("--precision mixed is measured as a whole loop: add --full-loop")
+        return run_mixed_loop(args, w, dev)
     prec = mm.MM_FP64 if args.precision == "fp64" else mm.MM_FP32
     tdt = torch.float64 if prec == mm.MM_FP64 else torch.float32
     esz = 8 if prec == mm.MM_FP64 else 4
@@ -454,6 +556,9 @@ def main():
     stream = torch.cuda.current_stream(dev)
     m = torch.from_numpy(w.initial_m()).to(device=dev, dtype=tdt).contiguous()
     flush = torch.empty(int(256 * 2**20) // 4, dtype=torch.float32, device=dev)  # > 2x L2
+
+    if args.full_loop:
+        return run_full_loop(args, w, prob, m, F, opts, stream, tdt, esz, info, dev)
 
     if args.profile_stages > 0:
         print(json.dumps(mm.mm_kernel_times(prob, m, F[0], reps=args.profile_stages, stream=stream)))

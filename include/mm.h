@@ -284,6 +284,27 @@ MM_API int mm_adjoint_dK(mm_problem *prob, const void *m, const double Hext[3], 
 MM_API int mm_set_anisotropy(mm_problem *prob, const double *K_cell, void *stream);
 
 /*
+ * mm_hysteresis_sweep_mixed -- the hysteresis driver of Section 4 in mixed
+ * precision (an extension; the paper uses one precision).  For every field
+ * value j >= start, the FP32 problem `lo` first minimises from the current
+ * state with opts_lo (a loose tolerance).  The FP64 problem `hi` then
+ * minimises from that result with opts_hi (the final tolerance).  The float
+ * phase does most of the descent at the float rate.  The double phase
+ * finishes the last decades of the stop rule, where float rounding slows the
+ * step-size rule down.  lo and hi must come from mm_setup_geometry with the
+ * same grid and material, precisions MM_FP32 and MM_FP64.
+ * m (host or device, [3][nz][ny][nx] float64, in/out) is the starting state;
+ * it receives the final one.  H_list, n, start, mavg as mm_hysteresis_sweep
+ * (mavg from the FP64 phase).  per_step_lo / per_step_hi (host, nullable,
+ * [n]) receive each phase's result; a float phase that stops at its
+ * iteration cap is not an error.  Returns MM_OK if every FP64 phase
+ * converged, else the first non-OK FP64 status.  Synchronises `stream`.
+ */
+MM_API int mm_hysteresis_sweep_mixed(mm_problem *lo, mm_problem *hi, void *m, const double *H_list, int n, int start,
+                                     const mm_min_opts *opts_lo, const mm_min_opts *opts_hi, double *mavg,
+                                     mm_min_result *per_step_lo, mm_min_result *per_step_hi, void *stream);
+
+/*
  * Batched sweeps (an extension; the paper sweeps one sample).  A batch
  * references existing problems (of any sizes and precisions; the caller keeps
  * owning them and must not destroy them while the batch exists) and runs

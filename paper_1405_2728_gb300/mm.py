@@ -92,6 +92,9 @@ def lib():
         L.mm_adjoint_dK.argtypes = [c_void_p, c_void_p, dp, c_void_p, c_void_p, c_double, c_long,
                                     POINTER(c_long), POINTER(c_double), c_void_p]
         L.mm_set_anisotropy.argtypes = [c_void_p, c_void_p, c_void_p]
+        L.mm_hysteresis_sweep_mixed.argtypes = [c_void_p, c_void_p, c_void_p, dp, c_int, c_int,
+                                                POINTER(mm_min_opts), POINTER(mm_min_opts), dp,
+                                                POINTER(mm_min_result), POINTER(mm_min_result), c_void_p]
         L.mm_batch_create.argtypes = [POINTER(c_void_p), c_int, POINTER(c_void_p)]
         L.mm_batch_destroy.argtypes = [c_void_p]
         L.mm_batch_sweep.argtypes = [c_void_p, POINTER(c_void_p), dp, c_int, c_int, POINTER(mm_min_opts), dp,
@@ -101,7 +104,7 @@ def lib():
         L.mm_last_cuda_error.restype = c_char_p
         for name in ("mm_newell", "mm_newell_static", "mm_setup_geometry", "mm_destroy", "mm_heff", "mm_energy", "mm_minimize",
                      "mm_hysteresis_sweep", "mm_problem_info", "mm_kernel_times", "mm_energy_gradient",
-                     "mm_hessian_vec", "mm_adjoint_dK", "mm_set_anisotropy", "mm_batch_create",
+                     "mm_hessian_vec", "mm_adjoint_dK", "mm_set_anisotropy", "mm_hysteresis_sweep_mixed", "mm_batch_create",
                      "mm_batch_destroy", "mm_batch_sweep"):
             getattr(L, name).restype = c_int
         _lib = L
@@ -279,6 +282,27 @@ def mm_hysteresis_sweep(prob: Problem, m, H_list, start=0, opts: mm_min_opts | N
     if st not in _SOFT:
         raise MMError(st, "mm_hysteresis_sweep")
     return st, mavg, list(res)
+
+
+def mm_hysteresis_sweep_mixed(lo: Problem, hi: Problem, m, H_list, start=0, opts_lo: mm_min_opts | None = None,
+                              opts_hi: mm_min_opts | None = None, stream=None, mavg=None):
+    """Mixed-precision sweep: per field value an FP32 minimisation (opts_lo,
+    loose tolerance) then an FP64 one (opts_hi).  m is float64 [3][nz][ny][nx].
+    Returns (status, mavg (n,3), [FP32 results], [FP64 results])."""
+    opts_lo = opts_lo or make_opts(tol=3e-5, max_iter=20000)
+    opts_hi = opts_hi or make_opts()
+    H = np.ascontiguousarray(np.asarray(H_list, dtype=np.float64).reshape(-1, 3))
+    n = H.shape[0]
+    if mavg is None:
+        mavg = np.full((n, 3), np.nan)
+    rl, rh = (mm_min_result * n)(), (mm_min_result * n)()
+    st = lib().mm_hysteresis_sweep_mixed(lo.handle, hi.handle, _ptr(m, np.float64, hi.shape, "m"),
+                                         H.ctypes.data_as(POINTER(c_double)), n, int(start), ctypes.byref(opts_lo),
+                                         ctypes.byref(opts_hi), mavg.ctypes.data_as(POINTER(c_double)), rl, rh,
+                                         _stream(stream, m))
+    if st not in _SOFT:
+        raise MMError(st, "mm_hysteresis_sweep_mixed")
+    return st, mavg, list(rl), list(rh)
 
 
 def mm_problem_info(prob: Problem) -> dict:
