@@ -100,7 +100,7 @@ def test_granular_cube_sweep_matches_oracle(mmlib):
     # +x, then rotates reversibly toward +x and back: no switching up to the
     # return to 0 T (the first 17 field values), so both loops agree value by
     # value there.  Under negative fields grains switch, and which one goes
-    # first is decided by rounding (R17); the loops are compared at their end.
+    # first is decided by rounding (the energy is non-convex); the loops are compared at their end.
     assert np.max(np.abs(mavg[:17] - mavg_ref[:17])) < 1e-5
     # the loops end saturated along -x on both sides
     assert abs(mavg[-1, 0] - mavg_ref[-1, 0]) < 1e-3
