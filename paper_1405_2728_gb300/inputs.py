@@ -211,4 +211,7 @@ WORKLOADS = {
 # bulk workloads (a different material and field protocol)
 BULK_WORKLOADS = {
     "cube_256": granular_cube,
+    # the same 512^3 padded grid with fewer cells (~2 GB on the device): the
+    # case the bulk kernels are profiled on
+    "cube_160": lambda: granular_cube(160, 64, edge=320e-9),
 }
