@@ -57,3 +57,21 @@ def test_mixed_rejects_mismatched_problems(mmlib):
         mmlib.mm_hysteresis_sweep_mixed(p32, p64, dev(w.initial_m()), w.fields()[:3])
     with pytest.raises(mmlib.MMError):  # precisions swapped
         mmlib.mm_hysteresis_sweep_mixed(p64, p64, dev(w.initial_m()), w.fields()[:3])
+
+
+def test_mixed_with_host_buffer_equals_device_buffer(mmlib):
+    # m may live in host memory: it is staged through the FP64 problem's buffers
+    w = inputs.film_32x16x1()
+    grid = mmlib.make_grid(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz)
+    mat = mmlib.make_material(w.Ms, w.A, w.K)
+    p64 = mmlib.mm_setup_geometry(grid, mat, mmlib.MM_FP64)
+    p32 = mmlib.mm_setup_geometry(grid, mat, mmlib.MM_FP32)
+    F = w.fields()[:12]
+    m_host = np.ascontiguousarray(w.initial_m())
+    st_h, mavg_h, _, rh_h = mmlib.mm_hysteresis_sweep_mixed(p32, p64, m_host, F)
+    m_dev = dev(w.initial_m())
+    st_d, mavg_d, _, rh_d = mmlib.mm_hysteresis_sweep_mixed(p32, p64, m_dev, F)
+    assert st_h == st_d == mmlib.MM_OK
+    assert np.array_equal(mavg_h, mavg_d)
+    assert np.array_equal(m_host, m_dev.cpu().numpy())
+    assert [r.heff_evals for r in rh_h] == [r.heff_evals for r in rh_d]
