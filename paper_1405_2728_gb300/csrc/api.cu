@@ -382,7 +382,12 @@ extern "C" int mm_setup_geometry(const mm_grid *grid, const mm_material *mat, in
         if (e) { mm_set_cuda_error(e, "setup"); rc = MM_ERR_CUDA; break; }
         if ((rc = mm_heff_configure(p)) != MM_OK) break;
         if (cudaMemsetAsync(p->mbuf[0], 0, F, s)) { rc = MM_ERR_CUDA; break; }
-        {
+        // Problems below 65 536 cells are launch-latency bound and their kernel
+        // times are mostly noise, so a timed choice would change from run to run.
+        // The shape changes the order of the partial sums, and through it the
+        // rounding that decides a minimiser's branch at a switching field.
+        // They keep the planner's defaults (largest tile, largest row batch).
+        if (p->g.N >= 65536) {
             NvtxRange nvtx_tune("mm_autotune");
             if ((rc = mm_autotune(p, p->tys, p->nty, p->rbs, p->nrb, s)) != MM_OK) break;
         }
