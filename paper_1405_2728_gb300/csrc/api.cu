@@ -144,9 +144,10 @@ int plan(mm_problem *p)
     g.fd_nc.init(g.stage ? gr.nx / 4 : 1);
     if (g.Px > 4096 || g.Py > 4096 || g.Pz > 4096) return MM_ERR_UNSUPPORTED;
     // padded shared-memory rows (one pad element per 8, see fft.cuh)
-    g.rsx = padded_row(g.Hx);
-    g.rsy = padded_row(g.Py);
-    g.rsz = padded_row(g.Pz);
+    const int vsz = p->precision == MM_FP32 ? 8 : 16;  // bytes per complex element
+    g.rsx = row_stride(g.Hx, vsz);
+    g.rsy = row_stride(g.Py, vsz);
+    g.rsz = row_stride(g.Pz, vsz);
     if (g.rsx <= g.Hx || g.rsy <= g.Py || g.rsz <= g.Pz) return MM_ERR_UNSUPPORTED;  // the kernels index rows with these strides
     g.lpz = ilog2i(g.Pz);
     g.Gz = g.Pz >= 8 ? g.Pz / 8 : 1;

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(BulkBound<T>::v) k_ypass(Geom g, FieldPtrs<T> 
             const int e = e0 + i * nth;
             if (e >= tot) break;
             const int c = e % 3, rest = e / 3, zl = rest / lin, y = rest - zl * lin;
-            S[(c * ZB + zl) * rs + pidx(y)] = v[i];
+            S[(c * ZB + zl) * rs + spos<V>(y)] = v[i];
         }
     }
     if (!INV) {
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(BulkBound<T>::v) k_ypass(Geom g, FieldPtrs<T> 
         for (int e = tid; e < 3 * zb * npad; e += nth) {
             const int r = e / npad, y = ny + (e - r * npad);
             const int c = r / zb, zl = r - c * zb;
-            S[(c * ZB + zl) * rs + pidx(y)] = czero<V>();
+            S[(c * ZB + zl) * rs + spos<V>(y)] = czero<V>();
         }
     }
     cp_async_wait_all();
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(BulkBound<T>::v) k_ypass(Geom g, FieldPtrs<T> 
     V *dst = INV ? P.W + first * ny * 3 : P.W2 + first * Py * 3;
     for (int e = tid; e < zb * lout * 3; e += nth) {
         const int c = e % 3, rest = e / 3, zl = rest / lout, y = rest - zl * lout;
-        dst[e] = S[(c * ZB + zl) * rs + pidx(y)];
+        dst[e] = S[(c * ZB + zl) * rs + spos<V>(y)];
     }
 }
 
@@ -115,14 +115,14 @@ __global__ void __launch_bounds__(BulkBound<T>::v) k_zconv(Geom g, FieldPtrs<T> 
             const int e = e0 + i * nth;
             if (e >= tot) break;
             const int c = e % 3, rest = e / 3, kyl = rest % kb, z = rest / kb;
-            S[(c * KB + kyl) * rs + pidx(z)] = v[i];
+            S[(c * KB + kyl) * rs + spos<V>(z)] = v[i];
         }
     }
     const int npad = Pz - nz;
     for (int e = tid; e < 3 * kb * npad; e += nth) {
         const int r = e / npad, z = nz + (e - r * npad);
         const int c = r / kb, kyl = r - c * kb;
-        S[(c * KB + kyl) * rs + pidx(z)] = czero<V>();
+        S[(c * KB + kyl) * rs + spos<V>(z)] = czero<V>();
     }
     cp_async_wait_all();
     __syncthreads();
@@ -145,9 +145,9 @@ __global__ void __launch_bounds__(BulkBound<T>::v) k_zconv(Geom g, FieldPtrs<T> 
         const T *n6 = Nk + ((long)kzr * (hy + 1) + kyr) * 6;
         const T nxx = __ldg(n6 + 0), nyy = __ldg(n6 + 1), nzz = __ldg(n6 + 2);
         const T nxy = sy * __ldg(n6 + 3), nxz = sz * __ldg(n6 + 4), nyz = sy * sz * __ldg(n6 + 5);
-        V *a0 = S + (0 * KB + kyl) * rs + pidx(kz);
-        V *a1 = S + (1 * KB + kyl) * rs + pidx(kz);
-        V *a2 = S + (2 * KB + kyl) * rs + pidx(kz);
+        V *a0 = S + (0 * KB + kyl) * rs + spos<V>(kz);
+        V *a1 = S + (1 * KB + kyl) * rs + spos<V>(kz);
+        V *a2 = S + (2 * KB + kyl) * rs + spos<V>(kz);
         const V m0 = *a0, m1 = *a1, m2 = *a2;
         V h0, h1, h2;
         h0.x = nxx * m0.x + nxy * m1.x + nxz * m2.x; h0.y = nxx * m0.y + nxy * m1.y + nxz * m2.y;
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(BulkBound<T>::v) k_zconv(Geom g, FieldPtrs<T> 
     __syncthreads();
     for (int e = tid; e < nz * kb * 3; e += nth) {
         const int c = e % 3, rest = e / 3, kyl = rest % kb, z = rest / kb;
-        base[(long)z * zs + kyl * 3 + c] = S[(c * KB + kyl) * rs + pidx(z)];
+        base[(long)z * zs + kyl * 3 + c] = S[(c * KB + kyl) * rs + spos<V>(z)];
     }
 }
 

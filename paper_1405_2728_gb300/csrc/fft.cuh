@@ -29,6 +29,27 @@ __host__ __device__ __forceinline__ int pidx(int i) { return i + (i >> 3); }
 // element so that consecutive rows start in different banks
 __host__ __device__ __forceinline__ int padded_row(int L) { return L + (L >> 3) + 1; }
 
+// Row layout by element size.  16-byte elements (double2) use the padding
+// above: each Stockham pass then takes the minimum number of shared-memory
+// wavefronts.  8-byte elements (float2) are served 16 per wavefront; with
+// the padding a warp's 32 consecutive elements span 36 slots, which costs 3
+// to 4 wavefronts instead of 2.  They use an XOR swizzle instead, within
+// aligned groups of 16 elements: bits 4-6 of the index are XORed into
+// bits 0-3 (bit 6 into bit 3).  In a bank simulation of the radix-8
+// Stockham passes this keeps unit-stride loads, the stride-8 stores of the
+// first pass and the grouped stores of the later passes at 2 wavefronts
+// (L = 512, 4096).  It is a permutation of every aligned group of 16, so a
+// row of L elements needs only L slots, plus one between rows.
+template <typename V> __host__ __device__ __forceinline__ int spos(int i)
+{
+    if constexpr (sizeof(V) == 8) return i ^ (((i >> 4) & 7) | (((i >> 6) & 1) << 3));
+    else return i + (i >> 3);
+}
+__host__ __device__ __forceinline__ int row_stride(int L, int esz)
+{
+    return esz == 8 ? L + 1 : padded_row(L);
+}
+
 // copy a twiddle table of n complex values into shared memory (all threads)
 template <typename V> __device__ __forceinline__ void load_twiddles(V *dst, const V *src, int n)
 {
@@ -138,7 +159,8 @@ __device__ __forceinline__ void stockham_pass(V *row, int L, int Ns, int j, int 
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if (HIN && r >= R / 2) { v[q * R + r] = czero<V>(); continue; }
-                v[q * R + r] = row[(LR & 7) ? pidx(b + r * LR) : p0 + r * ld9];
+                if constexpr (sizeof(V) == 8) v[q * R + r] = row[spos<V>(b + r * LR)];
+                else v[q * R + r] = row[(LR & 7) ? pidx(b + r * LR) : p0 + r * ld9];
             }
             if (Ns > 1) {
                 const int step = tstep0 * (b & (Ns - 1));
@@ -163,7 +185,8 @@ __device__ __forceinline__ void stockham_pass(V *row, int L, int Ns, int j, int 
 #pragma unroll
             for (int r = 0; r < (HOUT ? R / 2 : R); ++r) {
                 const int rn = r * Ns;
-                row[(R == 8) ? s0 + rn + (rn >> 3) : pidx(hi + k + rn)] = v[q * R + r];
+                if constexpr (sizeof(V) == 8) row[spos<V>(hi + k + rn)] = v[q * R + r];
+                else row[(R == 8) ? s0 + rn + (rn >> 3) : pidx(hi + k + rn)] = v[q * R + r];
             }
         }
     }

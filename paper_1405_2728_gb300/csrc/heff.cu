@@ -42,7 +42,7 @@ template <typename T> __device__ __forceinline__ T ldg(const T *p) { return __ld
 // real element x of a padded complex row holding Px reals
 template <typename T, typename V> __device__ __forceinline__ T &rel(V *row, int x)
 {
-    return reinterpret_cast<T *>(row + pidx(x >> 1))[x & 1];
+    return reinterpret_cast<T *>(row + spos<V>(x >> 1))[x & 1];
 }
 
 // Rows of a field [3][nz][ny][nx] copied asynchronously into shared memory:
@@ -165,8 +165,8 @@ __global__ void __launch_bounds__(768) k_xfwd(Geom g, FieldPtrs<T> P)
         const int c = e % 3, rest = e / 3, yl = rest & (TY - 1), k = rest >> g.ltyf;
         const int y = y0 + yl;
         const V *row = S + (c * TY + yl) * g.rsx;
-        const V Zk = row[pidx(k == Hx ? 0 : k)];
-        const V Zm = cconj(row[pidx(k == 0 ? 0 : Hx - k)]);
+        const V Zk = row[spos<V>(k == Hx ? 0 : k)];
+        const V Zm = cconj(row[spos<V>(k == 0 ? 0 : Hx - k)]);
         const V w = tw[k];
         const V sum = cadd(Zk, Zm), dif = csub(Zk, Zm);
         // X = (sum - i w dif) / 2
@@ -222,13 +222,13 @@ __global__ void __launch_bounds__(YZBound<T>::v) k_yz(Geom g, FieldPtrs<T> P)
             const int e = e0 + i * nth;
             if (e >= tot) break;
             const int c = e % 3, rest = e / 3, zz = g.fd_ny.div(rest), y = rest - zz * ny;
-            S[(c * nz + zz) * g.rsy + pidx(y)] = v[i];
+            S[(c * nz + zz) * g.rsy + spos<V>(y)] = v[i];
         }
     }
     const int npad = Py - ny;
     for (int e = tid; e < nrow * npad; e += nth) {
         const int row = g.fd_pady.div(e), y = ny + (e - row * npad);
-        S[row * g.rsy + pidx(y)] = czero<V>();
+        S[row * g.rsy + spos<V>(y)] = czero<V>();
     }
     cp_async_wait_all();
     __syncthreads();
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(YZBound<T>::v) k_yz(Geom g, FieldPtrs<T> P)
     const int hy = Py / 2, kst = hy + 1;
     const T *Kk = P.Nhat + (long)kx * NZM * 6 * kst;
     for (int ky = tid; ky < Py; ky += nth) {
-        const int pky = pidx(ky);
+        const int pky = spos<V>(ky);
         const int kyr = ky <= hy ? ky : Py - ky;
         const T sy = ky <= hy ? (T)1 : (T)-1;
         V mz[3][NZM], hz[3][NZM];
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(YZBound<T>::v) k_yz(Geom g, FieldPtrs<T> P)
 
     for (int e = tid; e < nrow * ny; e += nth) {
         const int c = e % 3, rest = e / 3, zz = g.fd_ny.div(rest), y = rest - zz * ny;
-        Wk[e] = S[(c * nz + zz) * g.rsy + pidx(y)];
+        Wk[e] = S[(c * nz + zz) * g.rsy + spos<V>(y)];
     }
 }
 
@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(768) k_xinv(Geom g, FieldPtrs<T> P, double hx0
             V Z;
             Z.x = sum.x - t.y;
             Z.y = sum.y + t.x;
-            S[(c * TY + yl) * g.rsx + pidx(kk)] = Z;
+            S[(c * TY + yl) * g.rsx + spos<V>(kk)] = Z;
         }
     }
     __syncthreads();
