@@ -110,3 +110,20 @@ def test_heff_full_film_512x256x4(mmlib):
     loc = (om.exchange_field(oprob, m) + om.anisotropy_field(oprob, m)).reshape(3, -1)[:, cells.astype(np.int64)]
     samp = Hd_direct + loc + np.asarray(Hext).reshape(3, 1)
     assert rel_l2(got.reshape(3, -1)[:, cells.astype(np.int64)], samp) <= 1e-10
+
+
+def test_largest_x_length_and_unsupported_grids(mmlib):
+    # nx = 2048 pads to Px = 4096, the largest supported x length; its FFT rows
+    # (length 2048) take the generic-length code path
+    prob, oprob = make_pair(mmlib, 2048, 2, 1, CELL)
+    m = inputs.random_unit_m(oprob.shape, seed=2048)
+    Hext = np.array([5e3, 1e3, 0.0])
+    H = torch.empty((3, 1, 2, 2048), dtype=torch.float64, device="cuda")
+    mmlib.mm_heff(prob, dev(m), Hext, H)
+    assert rel_l2(H.cpu().numpy(), om.heff(oprob, m, Hext, om.Demag(oprob))) <= 1e-10
+    # past any padded length of 4096: refused before anything is allocated or launched
+    mat = mmlib.make_material(8e5, 1.3e-11, 500.0)
+    for grid in ((2049, 2, 1), (4, 2049, 1), (4, 4, 2049)):
+        with pytest.raises(mmlib.MMError) as ei:
+            mmlib.mm_setup_geometry(mmlib.make_grid(*grid, *CELL), mat)
+        assert ei.value.status == mmlib.MM_ERR_UNSUPPORTED, grid
