@@ -91,3 +91,38 @@ def test_study_directions_and_sweep():
     assert met["H_sw"] * inputs.MU0 * 1e3 == -7.5
     assert -7.5 < met["H_c"] * inputs.MU0 * 1e3 < -7.0
     assert abs(met["M_r"][0] - np.tanh(7.25 / 2.0) * h[0]) < 1e-12
+
+
+def test_batch_films_ranges_and_determinism():
+    films = inputs.batch_films(64)
+    assert len(films) == 64
+    for w in films:
+        assert 64 <= w.nx <= 512 and 32 <= w.ny <= 256 and 1 <= w.nz <= 4
+        assert w.dx == w.dy == w.dz == 3.90625e-9 and 0.0 <= w.K < 2000.0
+        assert (w.max_mT, w.step_mT) == (50.0, 2.0) and w.fields().shape == (101, 3)
+    again = inputs.batch_films(64)
+    assert [(w.nx, w.ny, w.nz, w.K) for w in films] == [(w.nx, w.ny, w.nz, w.K) for w in again]
+    assert len({(w.nx, w.ny, w.nz) for w in films}) > 32  # uneven sizes
+
+
+def test_bench_algorithmic_model_film():
+    # pass-model bytes per kernel at 512x256x4 (F = 3 N s, W = 3 (Px/2+1) ny nz 2 s,
+    # T = 6 (Px/2+1) max(1, Pz/2) (Py/2+1) s)
+    import bench
+    nx, ny, nz, Px, Py, Pz = 512, 256, 4, 1024, 512, 8
+    for s in (8, 4):
+        F = 3 * nx * ny * nz * s
+        W = 3 * (Px // 2 + 1) * ny * nz * 2 * s
+        T = 6 * (Px // 2 + 1) * (Pz // 2) * (Py // 2 + 1) * s
+        info = {"nx": nx, "ny": ny, "nz": nz, "px": Px, "py": Py, "pz": Pz, "spectrum_bytes": W, "tensor_bytes": T,
+                "bulk_layout": 0}
+        mdl = bench.algorithmic_model(info, s)
+        assert mdl["xfwd_step"]["bytes"] == 3 * F + W
+        assert mdl["yz_conv"]["bytes"] == 2 * W + T
+        assert mdl["xinv_local_bb"]["bytes"] == W + 4 * F
+        if s == 8:  # 63 + 76 + 76 MB per iteration
+            assert [round(mdl[k]["bytes"] / 1e6) for k in ("xfwd_step", "yz_conv", "xinv_local_bb")] == [63, 76, 76]
+        assert all(v["flops"] > 0 for v in mdl.values())
+    info["bulk_layout"] = 1
+    mdl = bench.algorithmic_model(info, 4)
+    assert set(mdl) == {"xfwd_step", "y_fwd", "z_conv", "y_inv", "xinv_local_bb"}
