@@ -72,3 +72,43 @@ def test_binding_fails_loudly_without_the_library(monkeypatch):
     monkeypatch.setattr(mm, "LIB_PATH", "/nonexistent/libmmgb.so")
     with pytest.raises(ImportError):
         mm.lib()
+
+
+def test_every_entry_point_rejects_null_arguments(L):
+    """Each call checks its pointers and scalars before it touches the device."""
+    lib = L.lib()
+    h = (ctypes.c_double * 3)(0, 0, 0)
+    fake = ctypes.c_void_p(16)
+    opts = L.make_opts()
+    E = (ctypes.c_double * 5)()
+    mavg = (ctypes.c_double * 3)()
+    ARG = L.MM_ERR_ARG
+    assert lib.mm_energy(None, fake, h, E, None) == ARG
+    assert lib.mm_hysteresis_sweep(None, fake, h, 1, 0, ctypes.byref(opts), mavg, None, None) == ARG
+    assert lib.mm_energy_gradient(None, fake, h, 1.0, fake, None) == ARG
+    assert lib.mm_hessian_vec(None, fake, h, fake, fake, None) == ARG
+    assert lib.mm_adjoint_dK(None, fake, h, fake, fake, 1e-8, 100, None, None, None) == ARG
+    assert lib.mm_set_anisotropy(None, fake, None) == ARG
+    assert lib.mm_hysteresis_sweep_mixed(None, None, fake, h, 1, 0, ctypes.byref(opts), ctypes.byref(opts),
+                                         mavg, None, None, None) == ARG
+    out = ctypes.c_void_p()
+    assert lib.mm_batch_create(None, 1, ctypes.byref(out)) == ARG
+    assert out.value is None
+    assert lib.mm_batch_destroy(None) == L.MM_OK
+    assert lib.mm_batch_sweep(None, None, h, 1, 0, ctypes.byref(opts), mavg, None, None) == ARG
+    info = L.mm_info()
+    assert lib.mm_problem_info(None, ctypes.byref(info)) == ARG
+    ms = (ctypes.c_double * 8)()
+    names = (ctypes.c_char_p * 8)()
+    cnt = ctypes.c_int()
+    assert lib.mm_kernel_times(None, fake, h, 1, ms, names, ctypes.byref(cnt), None) == ARG
+    g = L.make_grid(4, 4, 1, 1e-9, 1e-9, 1e-9)
+    assert lib.mm_newell_static(ctypes.byref(g), None, None) == ARG
+    assert lib.mm_newell_static(None, fake, None) == ARG
+
+
+def test_newell_static_refuses_grids_past_its_buffer(L):
+    lib = L.lib()
+    big = L.make_grid(4096, 4096, 64, 1e-9, 1e-9, 1e-9)
+    assert lib.mm_newell_static(ctypes.byref(big), ctypes.c_void_p(16), None) == L.MM_ERR_UNSUPPORTED
+    assert isinstance(L.mm_status_string(L.MM_ERR_UNSUPPORTED), str)
