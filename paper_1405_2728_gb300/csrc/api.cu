@@ -143,7 +143,8 @@ int plan(mm_problem *p)
     g.stage = p->precision == MM_FP32 && gr.nx % 4 == 0;
     g.fd_nc.init(g.stage ? gr.nx / 4 : 1);
     if (g.Px > 4096 || g.Py > 4096 || g.Pz > 4096) return MM_ERR_UNSUPPORTED;
-    // padded shared-memory rows (one pad element per 8, see fft.cuh)
+    // shared-memory row strides: double rows pad one element per 8, float rows
+    // are XOR-swizzled within a stride of L+1 (fft.cuh)
     const int vsz = p->precision == MM_FP32 ? 8 : 16;  // bytes per complex element
     g.rsx = row_stride(g.Hx, vsz);
     g.rsy = row_stride(g.Py, vsz);
@@ -276,6 +277,15 @@ bool opts_ok(const mm_min_opts *o)
 
 bool vec_ok(const double *h) { return h && std::isfinite(h[0]) && std::isfinite(h[1]) && std::isfinite(h[2]); }
 
+// Record a failed runtime call and return rc.  Recording also reads the
+// runtime's last-error slot, so the failure does not resurface at the next
+// launch check.
+int failed(cudaError_t e, const char *where, int rc)
+{
+    mm_set_cuda_error(e, where);
+    return rc;
+}
+
 int status_of(int s)
 {
     switch (s) {
@@ -351,13 +361,17 @@ extern "C" int mm_setup_geometry(const mm_grid *grid, const mm_material *mat, in
             (rc = dalloc(p, (void **)&p->Hext_dev, 4 * sizeof(double))) ||
             (rc = dalloc(p, &p->stage_in, F)) || (rc = dalloc(p, &p->stage_out, F)))
             break;
-        if (cudaMallocHost((void **)&p->st_host, sizeof(MinState))) { rc = MM_ERR_OOM; break; }
-        if (cudaMemsetAsync(p->st, 0, sizeof(MinState), s) || cudaMemsetAsync(p->counter, 0, 64, s) || cudaMemsetAsync(p->gbuf[0], 0, F, s) ||
-            cudaMemsetAsync(p->gbuf[1], 0, F, s)) { rc = MM_ERR_CUDA; break; }
+        cudaError_t ce;
+        if ((ce = cudaMallocHost((void **)&p->st_host, sizeof(MinState)))) { rc = failed(ce, "cudaMallocHost", MM_ERR_OOM); break; }
+        if ((ce = cudaMemsetAsync(p->st, 0, sizeof(MinState), s)) || (ce = cudaMemsetAsync(p->counter, 0, 64, s)) ||
+            (ce = cudaMemsetAsync(p->gbuf[0], 0, F, s)) || (ce = cudaMemsetAsync(p->gbuf[1], 0, F, s))) {
+            rc = failed(ce, "cudaMemsetAsync", MM_ERR_CUDA);
+            break;
+        }
         // per-cell material, converted to the working precision
         if (mat->K_cell || mat->u_cell) {
             double *tmp = nullptr;
-            if (cudaMalloc((void **)&tmp, 3 * sizeof(double) * (size_t)g.N)) { rc = MM_ERR_OOM; break; }
+            if ((ce = cudaMalloc((void **)&tmp, 3 * sizeof(double) * (size_t)g.N))) { rc = failed(ce, "cudaMalloc", MM_ERR_OOM); break; }
             if (mat->K_cell && rc == MM_OK) {
                 if ((rc = dalloc(p, &p->Kc, (size_t)g.N * p->esz)) == MM_OK &&
                     (rc = copy_user(tmp, mat->K_cell, sizeof(double) * g.N, true, is_device_ptr(mat->K_cell), s)) == MM_OK)
@@ -374,7 +388,7 @@ extern "C" int mm_setup_geometry(const mm_grid *grid, const mm_material *mat, in
         }
         if ((rc = mm_launch_twiddles(p, s)) != MM_OK) break;
         double *Nd = nullptr;
-        if (cudaMalloc((void **)&Nd, sizeof(double) * 6 * (size_t)g.N)) { rc = MM_ERR_OOM; break; }
+        if ((ce = cudaMalloc((void **)&Nd, sizeof(double) * 6 * (size_t)g.N))) { rc = failed(ce, "cudaMalloc", MM_ERR_OOM); break; }
         rc = mm_newell_device(&p->grid, Nd, s);
         if (rc == MM_OK) rc = mm_tensor_spectrum(p, Nd, s);
         cudaError_t e = cudaStreamSynchronize(s);
@@ -382,7 +396,7 @@ extern "C" int mm_setup_geometry(const mm_grid *grid, const mm_material *mat, in
         if (rc != MM_OK) break;
         if (e) { mm_set_cuda_error(e, "setup"); rc = MM_ERR_CUDA; break; }
         if ((rc = mm_heff_configure(p)) != MM_OK) break;
-        if (cudaMemsetAsync(p->mbuf[0], 0, F, s)) { rc = MM_ERR_CUDA; break; }
+        if ((ce = cudaMemsetAsync(p->mbuf[0], 0, F, s))) { rc = failed(ce, "cudaMemsetAsync", MM_ERR_CUDA); break; }
         // Problems below 65 536 cells are launch-latency bound and their kernel
         // times are mostly noise, so a timed choice would change from run to run.
         // The shape changes the order of the partial sums, and through it the
