@@ -159,6 +159,17 @@ def _stream(stream, *arrays):
     return c_void_p(0)
 
 
+def _mavg(mavg, n):
+    """Per-field <m> output that the library writes on the host: a writable,
+    C-contiguous float64 numpy array (n, 3); a new one (NaN) when None."""
+    if mavg is None:
+        return np.full((n, 3), np.nan)
+    if (not isinstance(mavg, np.ndarray) or mavg.dtype != np.float64 or mavg.shape != (n, 3)
+            or not mavg.flags["C_CONTIGUOUS"] or not mavg.flags["WRITEABLE"]):
+        raise ValueError(f"mavg must be a writable C-contiguous float64 numpy array of shape ({n}, 3)")
+    return mavg
+
+
 def _vec3(h):
     v = np.ascontiguousarray(np.asarray(h, dtype=np.float64).reshape(3))
     return v, v.ctypes.data_as(POINTER(c_double))
@@ -273,8 +284,7 @@ def mm_hysteresis_sweep(prob: Problem, m, H_list, start=0, opts: mm_min_opts | N
     opts = opts or make_opts()
     H = np.ascontiguousarray(np.asarray(H_list, dtype=np.float64).reshape(-1, 3))
     n = H.shape[0]
-    if mavg is None:
-        mavg = np.full((n, 3), np.nan)
+    mavg = _mavg(mavg, n)
     res = (mm_min_result * n)()
     st = lib().mm_hysteresis_sweep(prob.handle, _ptr(m, prob.dtype, prob.shape, "m"),
                                    H.ctypes.data_as(POINTER(c_double)), n, int(start), ctypes.byref(opts),
@@ -293,8 +303,7 @@ def mm_hysteresis_sweep_mixed(lo: Problem, hi: Problem, m, H_list, start=0, opts
     opts_hi = opts_hi or make_opts()
     H = np.ascontiguousarray(np.asarray(H_list, dtype=np.float64).reshape(-1, 3))
     n = H.shape[0]
-    if mavg is None:
-        mavg = np.full((n, 3), np.nan)
+    mavg = _mavg(mavg, n)
     rl, rh = (mm_min_result * n)(), (mm_min_result * n)()
     st = lib().mm_hysteresis_sweep_mixed(lo.handle, hi.handle, _ptr(m, np.float64, hi.shape, "m"),
                                          H.ctypes.data_as(POINTER(c_double)), n, int(start), ctypes.byref(opts_lo),
@@ -397,6 +406,8 @@ def mm_batch_sweep(batch: Batch, m_list, H_list, start=0, opts: mm_min_opts | No
     H = np.ascontiguousarray(np.asarray(H_list, dtype=np.float64).reshape(-1, 3))
     n = H.shape[0]
     P = len(batch.probs)
+    if len(m_list) != P:
+        raise ValueError(f"m_list has {len(m_list)} fields for {P} problems")
     ptrs = (c_void_p * P)(*[_ptr(m, p.dtype, p.shape, "m") for m, p in zip(m_list, batch.probs)])
     mavg = np.full((P, n, 3), np.nan)
     res = (mm_min_result * (P * n))()

@@ -112,3 +112,31 @@ def test_newell_static_refuses_grids_past_its_buffer(L):
     big = L.make_grid(4096, 4096, 64, 1e-9, 1e-9, 1e-9)
     assert lib.mm_newell_static(ctypes.byref(big), ctypes.c_void_p(16), None) == L.MM_ERR_UNSUPPORTED
     assert isinstance(L.mm_status_string(L.MM_ERR_UNSUPPORTED), str)
+
+
+def test_binding_checks_host_outputs_before_the_call(L):
+    """Shapes, dtypes and lengths the library cannot check are checked in the
+    binding; a null problem handle then gets MM_ERR_ARG from the library."""
+    import numpy as np
+    prob = L.Problem(None, L.make_grid(4, 4, 1, 1e-9, 1e-9, 1e-9), L.MM_FP64)
+    m = np.zeros(prob.shape)
+    H = np.zeros((5, 3))
+    for bad in (np.zeros((4, 3)), np.zeros((5, 3), np.float32), np.zeros((3, 5)).T, np.zeros(15)):
+        with pytest.raises(ValueError):
+            L.mm_hysteresis_sweep(prob, m, H, mavg=bad)
+        with pytest.raises(ValueError):
+            L.mm_hysteresis_sweep_mixed(prob, prob, m, H, mavg=bad)
+    ro = np.zeros((5, 3))
+    ro.flags.writeable = False
+    with pytest.raises(ValueError):
+        L.mm_hysteresis_sweep(prob, m, H, mavg=ro)
+    with pytest.raises(L.MMError) as e:
+        L.mm_hysteresis_sweep(prob, m, H, mavg=np.zeros((5, 3)))
+    assert e.value.status == L.MM_ERR_ARG
+    with pytest.raises(TypeError):
+        L.mm_hysteresis_sweep(prob, m.astype(np.float32), H)
+    batch = L.Batch(None, [prob, prob])
+    with pytest.raises(ValueError):
+        L.mm_batch_sweep(batch, [m], H)
+    with pytest.raises(L.MMError):
+        L.mm_batch_sweep(batch, [m, m], H)
