@@ -312,7 +312,10 @@ MM_API int mm_hysteresis_sweep_mixed(mm_problem *lo, mm_problem *hi, void *m, co
  * minimiser loop (its CUDA graph, with the launch shapes its setup autotuner
  * chose) and gets a stream of its own; for every field value the batch issues
  * every problem's minimisation on its stream, so the problems run
- * concurrently on the GPU.
+ * concurrently on the GPU.  mm_batch_create returns MM_ERR_ARG for a null
+ * or repeated problem (one problem's buffers cannot serve two streams) and for
+ * one whose setup did not finish; the batch owns one stream and one event per
+ * problem, released by mm_batch_destroy.
  *
  * mm_batch_sweep: as mm_hysteresis_sweep for every problem i with the same
  * field list H_list[n][3] (host, A/m): m_list[i] (host or device, in/out) is

@@ -8,6 +8,7 @@
 // all streams in turn; the streams are independent, so the problems'
 // minimisations run concurrently and small films fill the GPU together.
 // The caller's stream is joined to all of them at the start and the end.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -51,6 +52,10 @@ int ensure_records(mm_problem *p, int n)
 extern "C" MM_API int mm_batch_create(mm_problem *const *probs, int n, mm_batch **out)
 {
     if (!probs || n < 1 || !out) return MM_ERR_ARG;
+    // a problem listed twice would run on two streams over one set of buffers
+    std::vector<mm_problem *> sorted(probs, probs + n);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return MM_ERR_ARG;
     for (int i = 0; i < n; ++i)
         if (!probs[i] || !probs[i]->graph_ready) return MM_ERR_ARG;
     mm_batch *b = new (std::nothrow) mm_batch;

@@ -140,3 +140,14 @@ def test_binding_checks_host_outputs_before_the_call(L):
         L.mm_batch_sweep(batch, [m], H)
     with pytest.raises(L.MMError):
         L.mm_batch_sweep(batch, [m, m], H)
+
+
+def test_batch_refuses_a_repeated_problem(L):
+    # the repeat is found before any problem is looked at, so placeholder
+    # handles suffice here
+    lib = L.lib()
+    out = ctypes.c_void_p()
+    same = (ctypes.c_void_p * 3)(16, 32, 16)
+    assert lib.mm_batch_create(same, 3, ctypes.byref(out)) == L.MM_ERR_ARG
+    assert out.value is None
+    assert lib.mm_batch_create(same, 0, ctypes.byref(out)) == L.MM_ERR_ARG
