@@ -109,3 +109,35 @@ def test_field_is_energy_gradient(percell):
         dU = (om.energy(prob, mp, Hext, d)["total"] - om.energy(prob, mm, Hext, d)["total"]) / (2 * h)
         Hfd = -dU / (om.MU0 * prob.Ms * prob.V)
         assert abs(Hfd - H[a, k, j, i]) <= 1e-7 * np.max(np.abs(H))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_uniform_cube_demag_energy_is_one_sixth(n):
+    # A uniformly magnetised cube has the body demagnetising factor 1/3 along
+    # every direction, so its demag energy is mu0 Ms^2 L^3 / 6 for any m,
+    # whatever the number of cells.
+    a = 4.0e-9
+    prob = om.Problem(n, n, n, a, a, a, Ms=8.0e5, A=1.3e-11, K=0.0)
+    for mdir in ([1.0, 0.0, 0.0], [0.0, 0.0, 1.0], [0.48, -0.6, 0.64]):
+        m = np.broadcast_to(np.reshape(mdir, (3, 1, 1, 1)), (3,) + prob.shape).copy()
+        E = om.energy(prob, m, (0, 0, 0), om.Demag(prob, workers=1))["demag"]
+        expect = om.MU0 * prob.Ms**2 * (n * a) ** 3 / 6.0
+        assert abs(E - expect) <= 1e-12 * expect
+
+
+@pytest.mark.parametrize("mdir,factor", [((1.0, 0.0, 0.0), -2.0), ((0.0, 1.0, 0.0), 1.0), ((0.0, 0.0, 1.0), 1.0)])
+def test_two_distant_cells_interact_as_point_dipoles(mdir, factor):
+    # Two cubic cells R apart along x, the cells between them empty (m = 0).
+    # E_d = two self energies (mu0 Ms^2 V / 6 each) plus the dipole-dipole
+    # energy mu0 Ms^2 V^2 (m1.m2 - 3 (m1.x)(m2.x)) / (4 pi R^3).  For cubes the
+    # first correction to the point dipole is of order (a/R)^4 (6.7e-6 here).
+    a, R = 5.0e-9, 16
+    prob = om.Problem(R + 1, 1, 1, a, a, a, Ms=8.0e5, A=1.3e-11, K=0.0)
+    m = np.zeros((3,) + prob.shape)
+    m[:, 0, 0, 0] = mdir
+    m[:, 0, 0, R] = mdir
+    E = om.energy(prob, m, (0, 0, 0), om.Demag(prob, workers=1))["demag"]
+    V = a**3
+    self_e = 2 * om.MU0 * prob.Ms**2 * V / 6.0
+    dip = om.MU0 * prob.Ms**2 * V * V * factor / (4 * math.pi * (R * a) ** 3)
+    assert abs((E - self_e) - dip) <= 2e-5 * abs(dip)
