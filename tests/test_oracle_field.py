@@ -141,3 +141,29 @@ def test_two_distant_cells_interact_as_point_dipoles(mdir, factor):
     self_e = 2 * om.MU0 * prob.Ms**2 * V / 6.0
     dip = om.MU0 * prob.Ms**2 * V * V * factor / (4 * math.pi * (R * a) ** 3)
     assert abs((E - self_e) - dip) <= 2e-5 * abs(dip)
+
+
+@pytest.mark.parametrize("axis", ["y", "z"])
+def test_exchange_spiral_along_y_and_z(axis):
+    # The spiral closed form along each of the other axes, with cell sizes
+    # that differ per axis (3, 4, 5 nm): catches a cell size taken from the
+    # wrong axis, which the energy-gradient check alone would not.
+    q = 0.25
+    shape = {"y": (2, 12, 3), "z": (3, 2, 10)}[axis]  # nx, ny, nz
+    prob = _prob(*shape, K=0.0)
+    n_ax, d, ax = {"y": (shape[1], prob.dy, 2), "z": (shape[2], prob.dz, 1)}[axis]
+    ang = q * np.arange(n_ax)
+    m = np.zeros((3,) + prob.shape)
+    bshape = [1, 1, 1]
+    bshape[ax - 1] = n_ax
+    m[0] = np.broadcast_to(np.cos(ang).reshape(bshape), prob.shape)
+    m[2] = np.broadcast_to(np.sin(ang).reshape(bshape), prob.shape)
+    E = om.energy(prob, m, (0, 0, 0), om.Demag(prob, workers=1))["exchange"]
+    bonds = prob.nx * prob.ny * prob.nz // n_ax * (n_ax - 1)
+    expect = prob.A * prob.V * bonds * (2 - 2 * math.cos(q)) / d**2
+    assert abs(E - expect) <= 1e-13 * expect
+    H = om.exchange_field(prob, m)
+    c = 2 * prob.A / (om.MU0 * prob.Ms) * (2 * math.cos(q) - 2) / d**2
+    inner = [slice(None)] * 4
+    inner[ax] = slice(1, -1)
+    assert np.allclose(H[tuple(inner)], c * m[tuple(inner)], rtol=1e-12, atol=1e-6)
