@@ -4,13 +4,15 @@ sweep on the 2000 x 1000 x 20 nm film (512 x 256 x 4 cells), one GB300.
 A step is one field value of the sweep: set the field, minimise to the stop
 rule (max |m x H| / Ms < 1e-5) from the previous state -- the whole device
 path: x-FFT with the fused step, y-z convolution, x-inverse with the local
-terms and BB sums, the one-CTA step-size kernel, looped on the device by a CUDA
-graph.  `value` = effective-field evaluations per second over the K timed
+terms and BB sums (its last CTA picks the step size and applies the stop
+rule), looped on the device by a CUDA graph.  `value` = effective-field evaluations per second over the K timed
 steps (inputs resident in HBM), L2 flushed between steps.  `e2e` is the same
 through the C ABI with the magnetisation in pinned host memory (copied in and
 out inside every step).  Under torchrun each rank runs an independent replica
 (a single minimisation does not shard); value sums the ranks' evaluations over
-the slowest rank's time.
+the slowest rank's time.  By default the line also carries the other
+precision (FP32 beside FP64) on the same field values, each with the roofline
+of its dominant kernel.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
   python bench.py --impl reference   # the CPU oracle on the same workload and metric
@@ -33,10 +35,9 @@ if ROOT not in sys.path:
 METRIC = "H_eff evals/s & hysteresis-loop time (512x256x4 film) FP32 vs FP64, %HBM peak"
 UNIT = "H_eff evals/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 FMA lanes per SM per clock on GB300 (1.25 TFLOP/s at 2070 MHz over 152 SMs, 2 flops per FMA)
+# nominal FMA lanes per SM per clock (the measured rates come from mm_probe_fma)
 FP64_FMA_PER_SM_CLK = 2
 FP32_FMA_PER_SM_CLK = 128
-N_SM = 152
 
 
 def dist_env():
@@ -110,7 +111,7 @@ class ClockSampler:
 
 
 def algorithmic_model(info, esz):
-    """Bytes and flops per launch of each kernel stage (pass model; see the design notes).
+    """Bytes and flops per launch of each kernel stage as the kernels run them.
 
     Bytes: compulsory traffic of the pass structure -- xfwd reads m_k and g_k
     and writes m_{k+1} and the x-spectrum; yz reads/writes the spectrum and
@@ -172,6 +173,33 @@ def algorithmic_model(info, esz):
         f_yz = C * (3 * nz * (fft_flops(Py, True, False) + fft_flops(Py, False, True)) + Py * zc)
         model["yz_conv"] = {"bytes": 2 * W + T, "flops": f_yz}
     return model
+
+
+def survey_flops(info):
+    """Flops per launch of each stage under the workload's reference flop
+    model: 2.5 L log2 L per real and 5 L log2 L per complex transform of
+    length L (padded), 36 flops per frequency for the symmetric tensor
+    product, 200 flops per cell for the local terms, torque, step and
+    step-size sums.  At 512 x 256 x 4 (padded 1024 x 512 x 8) this is
+    x 0.157 + y 0.284 + z 0.189 + product 0.076 + local 0.105 = 0.81 GFLOP per
+    evaluation.  The kernels execute fewer flops (zero inputs and discarded
+    outputs pruned, the film z direction as a direct sum); this model is the
+    algorithmic count the roofline is quoted against."""
+    import math
+    nx, ny, nz, Px, Py, Pz = (info[k] for k in ("nx", "ny", "nz", "px", "py", "pz"))
+    C = Px // 2 + 1
+    lg = lambda L: math.log2(L) if L > 1 else 0.0
+    x_half = 3 * ny * nz * 2.5 * Px * lg(Px)          # one real transform per row
+    y_one = 3 * C * nz * 5 * Py * lg(Py)              # one direction of the y transforms
+    z_both = 2 * 3 * C * Py * 5 * Pz * lg(Pz)
+    prod = 36 * C * Py * Pz
+    local = 200 * nx * ny * nz
+    out = {"xfwd_step": x_half, "xinv_local_bb": x_half + local}
+    if info.get("bulk_layout"):
+        out.update({"y_fwd": y_one, "z_conv": z_both + prod, "y_inv": y_one})
+    else:
+        out["yz_conv"] = 2 * y_one + z_both + prod
+    return out
 
 
 KERNEL_SOURCES = ("common.cuh", "fft.cuh", "heff.cu")  # what the three film field kernels compile from
@@ -465,6 +493,9 @@ def run_batch(args, ws, rank, local, dev):
 
 
 def run_reference(args, ws, rank):
+    """The oracle as it stands, on this host's cores: one minimisation of
+    K iterations at the workload's first field value (tol 0, so it never
+    stops early), every field evaluation counted, after W untimed ones."""
     if rank != 0:
         return 0
     from paper_1405_2728_gb300 import inputs
@@ -479,22 +510,20 @@ def run_reference(args, ws, rank):
     demag = om.Demag(oprob, workers=workers)
     m = w.initial_m()
     H = w.fields()[0]
-    for _ in range(args.warmup):
-        m = om.minimize(oprob, m, H, demag, tol=0.0, max_iter=1).m
+    m = om.minimize(oprob, m, H, demag, tol=0.0, max_iter=args.warmup - 1).m   # W evaluations
     t0 = time.perf_counter()
-    evals = 0
-    for _ in range(args.steps):   # each step: one minimiser iteration (one evaluation + step)
-        r = om.minimize(oprob, m, H, demag, tol=0.0, max_iter=1)
-        m = r.m
-        evals += r.heff_evals - 1
+    r = om.minimize(oprob, m, H, demag, tol=0.0, max_iter=args.steps)       # K steps: K + 1 evaluations
     dt = time.perf_counter() - t0
+    evals = r.heff_evals
     value = evals / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": w.name, "cells": [w.nx, w.ny, w.nz], "precision": args.precision},
+            "data": "synthetic", "config": {"workload": w.name, "cells": [w.nx, w.ny, w.nz], "precision": args.precision,
+                                            "step": "one oracle minimiser iteration (field evaluation + step)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
-                             "sample": f"{args.steps} oracle minimiser iterations (H_eff + step) at {w.name}"},
+                             "sample": f"one oracle minimisation of {args.steps} iterations ({evals} field "
+                                       f"evaluations) at {w.name}, first field value"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -511,6 +540,8 @@ def main():
     ap.add_argument("--mixed-tol", type=float, default=3e-5)
     ap.add_argument("--workload", default="film_512x256x4")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", action="store_true",
+                    help="measure only --precision (by default the line also carries the other precision)")
     ap.add_argument("--full-loop", action="store_true",
                     help="time one whole hysteresis loop (every field value, one sweep call) instead of K steps")
     ap.add_argument("--max-iter", type=int, default=200000,
@@ -565,38 +596,42 @@ def main():
         prob.close()
         return 0
 
-    def field_step(buf, i):
-        st, _, res = mm.mm_hysteresis_sweep(prob, buf, F[: i + 1], start=i, opts=opts, stream=stream)
+    def field_step(p, buf, i):
+        st, _, res = mm.mm_hysteresis_sweep(p, buf, F[: i + 1], start=i, opts=opts, stream=stream)
         return st, res[i]
 
+    def timed_steps(p, buf, first, K):
+        """K field values starting at index `first`, L2 flushed before each,
+        CUDA events around each on the launching stream."""
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        n_ev = n_launch = 0
+        sts = []
+        torch.cuda.synchronize()
+        for j in range(K):
+            flush.zero_()
+            evs[j][0].record(stream)
+            st, r = field_step(p, buf, (first + j) % len(F))
+            evs[j][1].record(stream)
+            n_ev += r.heff_evals
+            n_launch += r.kernel_launches
+            sts.append(st)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs), n_ev, n_launch, sts
+
     for i in range(args.warmup):
-        field_step(m, i)
+        field_step(prob, m, i)
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
 
     K = args.steps
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    evals = launches = 0
-    statuses = []
     sampler = ClockSampler(local)
     t_wall = time.perf_counter()
     with sampler:
-        torch.cuda.synchronize()
-        for j in range(K):
-            i = (args.warmup + j) % len(F)
-            flush.zero_()
-            evs[j][0].record(stream)
-            st, r = field_step(m, i)
-            evs[j][1].record(stream)
-            evals += r.heff_evals
-            launches += r.kernel_launches
-            statuses.append(st)
-        torch.cuda.synchronize()
+        ms, evals, launches, statuses = timed_steps(prob, m, args.warmup, K)
     t_wall = time.perf_counter() - t_wall
     if ws > 1:
         dist.barrier()
-    ms = sum(a.elapsed_time(b) for a, b in evs)
     clocks = sampler.summary()
 
     # end to end through the C ABI with the magnetisation in pinned host memory
@@ -609,38 +644,59 @@ def main():
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st, r = field_step(mh, i)   # host buffer: H2D in, minimise, D2H out inside the call
+        st, r = field_step(prob, mh, i)   # host buffer: H2D in, minimise, D2H out inside the call
         e2e_ms += 1e3 * (time.perf_counter() - t0)
         e2e_evals += r.heff_evals
-
-    # per-kernel device times for the roofline
-    ktimes = mm.mm_kernel_times(prob, m, F[args.warmup], reps=30, stream=stream)
-    model = algorithmic_model(info, esz)
 
     evals_all, ms_max, e2e_all, e2e_max = combine_ranks(evals, ms, e2e_evals, e2e_ms, ws, dev)
     if rank != 0:
         dist.destroy_process_group() if ws > 1 else None
         return 0
 
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = measured_peaks()
+    fma = mm.mm_probe_fma()
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
+
+    def roofline(p, pname, buf, at_field):
+        """Roofline of the dominant kernel stage of problem p: per-stage CUDA
+        event times over 30 repetitions on the launching stream."""
+        kt = mm.mm_kernel_times(p, buf, F[at_field], reps=30, stream=stream)
+        inf = mm.mm_problem_info(p)
+        e = 8 if pname == "fp64" else 4
+        model = algorithmic_model(inf, e)
+        sflops = survey_flops(inf)
+        dom = max(kt, key=kt.get)
+        sec = kt[dom] * 1e-3
+        gbs = model[dom]["bytes"] / sec / 1e9
+        hbm = peaks.get("hbm_gbs")
+        if pname == "fp64":
+            derived = n_sm * FP64_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12
+            peak = fma["fp64"]
+            ach = sflops[dom] / sec / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                    "peak_source": f"measured FP64 FMA throughput (mm_probe_fma, {n_sm} SMs): {peak:.3f} TFLOP/s; "
+                                   f"nominal {n_sm} SMs x {FP64_FMA_PER_SM_CLK} FMA/clk x 2 flop at "
+                                   f"{sm_mhz:.0f} MHz = {derived:.3f}",
+                    "flop_model": "workload reference model (2.5/5 L log2 L per real/complex transform, 36 per "
+                                  "frequency, 200 per cell)",
+                    "executed_flops_frac": model[dom]["flops"] / sec / 1e12 / peak}
+        else:
+            peak = hbm or 6800.0
+            roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                    "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)" if hbm else "fallback 6.8 TB/s",
+                    "fp32_alu_frac": sflops[dom] / sec / 1e12 / fma["fp32"]}
+        roof["kernel"] = dom
+        roof["traffic"] = load_traffic(dom, w.name, pname)
+        roof["algorithmic_bytes"] = model[dom]["bytes"]
+        roof["algorithmic_flops"] = sflops[dom]
+        roof["hbm_frac_of_measured"] = gbs / (hbm or 6800.0)
+        roof["stage_ms"] = kt
+        return roof, kt
+
     value = evals_all / (ms_max / 1e3)
     e2e_value = e2e_all / (e2e_max / 1e3)
-    dom = max(ktimes, key=ktimes.get)
-    peaks = measured_peaks()
-    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
-    if prec == mm.MM_FP64:
-        peak = N_SM * FP64_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
-        achieved = model[dom]["flops"] / (ktimes[dom] * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": f"FP64 FMA: {N_SM} SMs x {FP64_FMA_PER_SM_CLK} FMA/clk x 2 flop at {sm_mhz:.0f} MHz"}
-    else:
-        peak = peaks.get("hbm_gbs", 6800.0)
-        achieved = model[dom]["bytes"] / (ktimes[dom] * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)" if "hbm_gbs" in peaks else "fallback"}
-    roof["kernel"] = dom
-    roof["traffic"] = load_traffic(dom, w.name, args.precision)
-    roof["hbm_frac_of_measured"] = model[dom]["bytes"] / (ktimes[dom] * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0)
-    roof["stage_ms"] = ktimes
+    roof, ktimes = roofline(prob, args.precision, m, args.warmup)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
@@ -660,7 +716,28 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clocks,
         "roofline": roof,
+        "n_sm": n_sm,
+        "fma_peaks_tflops": fma,
     }
+    # the other precision of the metric on the same workload and field values
+    other = [] if args.only else [q for q in ("fp64", "fp32") if q != args.precision]
+    for q in other:
+        qprec = mm.MM_FP64 if q == "fp64" else mm.MM_FP32
+        qdt = torch.float64 if q == "fp64" else torch.float32
+        qp = mm.mm_setup_geometry(grid, mm.make_material(w.Ms, w.A, w.K, K_cell=w.K_cell, u_cell=w.u_cell), qprec)
+        qm = torch.from_numpy(w.initial_m()).to(device=dev, dtype=qdt).contiguous()
+        for i in range(args.warmup):
+            field_step(qp, qm, i)
+        qsampler = ClockSampler(local)
+        with qsampler:
+            qms, qev, qla, qst = timed_steps(qp, qm, args.warmup, K)
+        qroof, _ = roofline(qp, q, qm, args.warmup)
+        qinfo = mm.mm_problem_info(qp)
+        line[q] = {"value": qev / (qms / 1e3), "unit": UNIT, "dtype": "f64" if q == "fp64" else "f32",
+                   "ms_per_step": qms / K, "evals_per_step": qev / K, "statuses": qst, "gpu_launches": int(qla),
+                   "loop_time_s_est": len(F) * (qms / K) / 1e3, "roofline": qroof, "clocks": qsampler.summary(),
+                   "launch_shape": {k: qinfo[k] for k in ("x_fwd_tile_rows", "x_tile_rows", "yz_batch_rows")}}
+        qp.close()
     if ws == 1:
         ours = sum(ktimes.values())
         theirs = cufft_demag_ms(info, tdt, dev)

@@ -114,8 +114,9 @@ MM_API int mm_newell(const mm_grid *grid, double *N_out, void *stream);
  * It calls no allocating routine: its double-double work table is a static
  * device array of 6 MiB compiled into the library, held by every GPU that
  * loads it until the process exits.
- * N_dev: DEVICE memory only (host pointers return MM_ERR_ARG), double,
- * [6][nz][ny][nx], same layout and values as mm_newell.
+ * N_dev: DEVICE memory of the current device only (host pointers, and
+ * device memory of another GPU, return MM_ERR_ARG), double, [6][nz][ny][nx],
+ * same layout and values as mm_newell.
  * Limit: (nx+1)(ny+1)(nz+1) <= 65536 lattice points (e.g. 255 x 127 x 1,
  * 63 x 63 x 15); larger grids return MM_ERR_UNSUPPORTED and launch nothing.
  * Asynchronous on `stream`; returns after launching (launch errors give
@@ -356,6 +357,16 @@ MM_API int mm_problem_info(const mm_problem *prob, mm_info *info);
  */
 MM_API int mm_kernel_times(mm_problem *prob, const void *m, const double Hext[3], int reps, double *ms_out,
                     const char **names, int *count, void *stream);
+
+/*
+ * mm_probe_fma -- instrumentation: measured fused-multiply-add throughput of
+ * the current device, tflops_out (host) [2] = FP64, FP32 in TFLOP/s (2 flops
+ * per FMA), from independent FMA chains filling every SM, best of three ~5 ms
+ * launches on the legacy default stream.  The double-precision field kernels
+ * are bound by the FP64 units, so this is their roofline peak.  Allocates a
+ * small buffer; synchronises the device.  (Instrumentation; not in the paper.)
+ */
+MM_API int mm_probe_fma(double tflops_out[2]);
 
 /* Human-readable text of a status code (static string). */
 MM_API const char *mm_status_string(int status);

@@ -25,9 +25,14 @@ definitions of the energy terms, as plainly as possible:
 * hysteresis driver, Section 4: one minimisation per field value, warm-started
   from the previous magnetisation.
 
-Readings of points where the paper is silent or garbled (sign of the step,
-alternation order, stop quantity, tau0, boundary condition, ...) are listed in
-the design notes of the repository and restated at each function below.
+Where the paper is silent or garbled, the readings taken are stated at the
+function they affect: the descent sign of the step and the printed sign slip
+of the projection (``projected_gradient``, ``cayley_step``), the alternation
+order and the fallback for non-positive curvature (``bb_tau``), the first step
+size tau0 = 1e-2/Ms and the stop quantity max|m x H|/Ms evaluated before
+stepping (``minimize``), the restart of the step-size history at every field
+value (``sweep``), the free exchange boundary (``exchange_field``) and
+mu0 = 4 pi 1e-7 exactly (``MU0``).
 
 Arrays: a vector field is float64 of shape (3, nz, ny, nx) (x fastest).
 """

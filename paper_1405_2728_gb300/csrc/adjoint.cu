@@ -118,7 +118,7 @@ __global__ void k_dJdK(const T *m, const T *lam, const T *uc, double u0, double 
     }
 }
 
-int grid_for(long n) { long b = (n + 255) / 256; return (int)(b < 152 * 8 ? (b > 0 ? b : 1) : 152 * 8); }
+int grid_for(long n) { return mm_grid_for(n, 256, 8); }
 
 struct Scratch {
     double *partials = nullptr, *scalars = nullptr, *scalars_host = nullptr;

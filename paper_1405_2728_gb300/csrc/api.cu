@@ -86,6 +86,29 @@ bool mm_is_device_ptr(const void *ptr)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+int mm_sm_count()
+{
+    static int cached[256];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) { cudaGetLastError(); return 1; }
+    if (!cached[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+            cudaGetLastError();
+            return 1;
+        }
+        cached[dev] = n;
+    }
+    return cached[dev];
+}
+
+int mm_grid_for(long n, int threads, int per_sm)
+{
+    const long want = (n + threads - 1) / threads;
+    const long cap = (long)mm_sm_count() * per_sm;
+    return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
 namespace {
 #define is_device_ptr mm_is_device_ptr
 

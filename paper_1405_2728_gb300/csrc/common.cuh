@@ -277,6 +277,11 @@ int mm_tensor_spectrum(mm_problem *p, const double *N_dev, cudaStream_t s);
 
 // helpers (api.cu)
 bool mm_is_device_ptr(const void *ptr);
+// streaming multiprocessors of the current device (queried once per device)
+int mm_sm_count();
+// grid of a grid-stride loop over n elements with `threads` per CTA: enough
+// CTAs for n, at most `per_sm` resident CTAs on every SM of the device
+int mm_grid_for(long n, int threads, int per_sm);
 int mm_copy_user(void *dst, const void *src, size_t bytes, bool dst_dev, bool src_dev, cudaStream_t s);
 // error bookkeeping (api.cu)
 void mm_set_cuda_error(cudaError_t e, const char *where);

@@ -1095,7 +1095,7 @@ int mm_launch_record(mm_problem *p, int step, cudaStream_t s)
 int mm_launch_copy_result(mm_problem *p, void *dst, cudaStream_t s)
 {
     const long n3 = 3 * p->g.N;
-    const int blocks = (int)((n3 + 255) / 256 < 152 * 8 ? (n3 + 255) / 256 : 152 * 8);
+    const int blocks = mm_grid_for(n3, 256, 8);
     if (p->precision == MM_FP64)
         k_copy_result<double><<<blocks, 256, 0, s>>>(p->st, (const double *)p->mbuf[0],
                                                     (const double *)p->mbuf[1], (double *)dst, n3);
@@ -1124,7 +1124,7 @@ int mm_launch_twiddles(mm_problem *p, cudaStream_t s)
 
 int mm_launch_convert(mm_problem *p, void *dst, const double *src, long n, cudaStream_t s)
 {
-    const int blocks = (int)((n + 255) / 256 < 1216 ? (n + 255) / 256 : 1216);
+    const int blocks = mm_grid_for(n, 256, 8);
     if (p->precision == MM_FP64) k_convert<double><<<blocks, 256, 0, s>>>((double *)dst, src, n);
     else k_convert<float><<<blocks, 256, 0, s>>>((float *)dst, src, n);
     cudaError_t e = cudaGetLastError();

@@ -32,7 +32,7 @@ __global__ void k_transfer(const MinState *st, const S *b0, const S *b1, D *dst,
 int transfer(mm_problem *from, mm_problem *to, cudaStream_t s)
 {
     const long n3 = 3 * from->g.N;
-    const int blocks = (int)((n3 + 255) / 256 < 152 * 8 ? (n3 + 255) / 256 : 152 * 8);
+    const int blocks = mm_grid_for(n3, 256, 8);
     if (from->precision == MM_FP64)
         k_transfer<double, float><<<blocks, 256, 0, s>>>(from->st, (const double *)from->mbuf[0],
                                                          (const double *)from->mbuf[1], (float *)to->mbuf[0], n3);

@@ -185,10 +185,12 @@ int mm_newell_device(const mm_grid *gr, double *N_dev, cudaStream_t s)
     if (e) { mm_set_cuda_error(e, "cudaMallocAsync(newell table)"); return MM_ERR_OOM; }
     const int bt = 128;
     long blocks = (na + bt - 1) / bt;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks > mm_sm_count() * 64L) blocks = mm_sm_count() * 64L;
     k_newell_table<<<(int)blocks, bt, 0, s>>>(gr->nx, gr->ny, gr->nz, hx, hy, hz, T);
+    e = cudaGetLastError();
+    if (e) { mm_set_cuda_error(e, "mm_newell_static table kernel"); return MM_ERR_CUDA; }
     blocks = (nn + bt - 1) / bt;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks > mm_sm_count() * 64L) blocks = mm_sm_count() * 64L;
     k_newell_stencil<<<(int)blocks, bt, 0, s>>>(gr->nx, gr->ny, gr->nz, hx, hy, hz, T, N_dev);
     e = cudaGetLastError();
     cudaFreeAsync(T, s);
@@ -222,16 +224,16 @@ int mm_tensor_spectrum(mm_problem *p, const double *N_dev, cudaStream_t s)
     const long outer[3] = {g.Px, (long)g.Px * g.Py, 0};
     const double2 *tws[3] = {twx, twy, twz};
     long blocks = (tot + 255) / 256;
-    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks > mm_sm_count() * 32L) blocks = mm_sm_count() * 32L;
     const long ext = (long)(g.Px / 2 + 1) * (g.Py / 2 + 1) * (g.Pz / 2 + 1);
     long eblocks = (ext + 255) / 256;
-    if (eblocks > 152 * 32) eblocks = 152 * 32;
+    if (eblocks > mm_sm_count() * 32L) eblocks = mm_sm_count() * 32L;
     // film layout: transforms along x and y only (the film kernel convolves z directly)
     const int naxes = g.bulk ? 3 : 2;
     const int nzf = g.Pz > 1 ? g.Pz / 2 : 1;
     const long fext = (long)(g.Px / 2 + 1) * nzf * (g.Py / 2 + 1);
     long fblocks = (fext + 255) / 256;
-    if (fblocks > 152 * 32) fblocks = 152 * 32;
+    if (fblocks > mm_sm_count() * 32L) fblocks = mm_sm_count() * 32L;
     for (int c = 0; c < 6 && !e; ++c) {
         k_place<<<(int)blocks, 256, 0, s>>>(c, g.nx, g.ny, g.nz, g.Px, g.Py, g.Pz, N_dev, F);
         for (int a = 0; a < naxes; ++a) {
@@ -290,7 +292,8 @@ extern "C" MM_API int mm_newell_static(const mm_grid *gr, double *N_dev, void *s
     if (!gr || !N_dev || gr->nx < 1 || gr->ny < 1 || gr->nz < 1 || !(gr->dx > 0) || !(gr->dy > 0) ||
         !(gr->dz > 0) || !isfinite(gr->dx) || !isfinite(gr->dy) || !isfinite(gr->dz))
         return MM_ERR_ARG;
-    const long na = (long)(gr->nx + 1) * (gr->ny + 1) * (gr->nz + 1);
+    // lattice points in 64-bit arithmetic: nx + 1 must not overflow int
+    const long na = ((long)gr->nx + 1) * ((long)gr->ny + 1) * ((long)gr->nz + 1);
     if (na > MM_NEWELL_STATIC_POINTS) return MM_ERR_UNSUPPORTED;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, N_dev) != cudaSuccess) { cudaGetLastError(); return MM_ERR_ARG; }
@@ -299,6 +302,8 @@ extern "C" MM_API int mm_newell_static(const mm_grid *gr, double *N_dev, void *s
     cudaError_t e = cudaGetDevice(&dev);
     if (e) { mm_set_cuda_error(e, "cudaGetDevice"); return MM_ERR_CUDA; }
     if (dev < 0 || dev >= 256) return MM_ERR_UNSUPPORTED;
+    // the kernels run on the current device: the output must live there
+    if (a.type == cudaMemoryTypeDevice && a.device != dev) return MM_ERR_ARG;
     dd_t *T = nullptr;
     {
         // first call on this device: look up the device address of the table
@@ -320,11 +325,13 @@ extern "C" MM_API int mm_newell_static(const mm_grid *gr, double *N_dev, void *s
     cudaStream_t s = (cudaStream_t)stream;
     const int bt = 128;
     long blocks = (na + bt - 1) / bt;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks > mm_sm_count() * 64L) blocks = mm_sm_count() * 64L;
     // every table entry read by the stencil is written first, so nothing needs clearing
     k_newell_table<<<(int)blocks, bt, 0, s>>>(gr->nx, gr->ny, gr->nz, hx, hy, hz, T);
+    e = cudaGetLastError();
+    if (e) { mm_set_cuda_error(e, "mm_newell_static table kernel"); return MM_ERR_CUDA; }
     blocks = (nn + bt - 1) / bt;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks > mm_sm_count() * 64L) blocks = mm_sm_count() * 64L;
     k_newell_stencil<<<(int)blocks, bt, 0, s>>>(gr->nx, gr->ny, gr->nz, hx, hy, hz, T, N_dev);
     e = cudaGetLastError();
     if (e) { mm_set_cuda_error(e, "mm_newell_static kernels"); return MM_ERR_CUDA; }

@@ -95,6 +95,7 @@ def lib():
         L.mm_hysteresis_sweep_mixed.argtypes = [c_void_p, c_void_p, c_void_p, dp, c_int, c_int,
                                                 POINTER(mm_min_opts), POINTER(mm_min_opts), dp,
                                                 POINTER(mm_min_result), POINTER(mm_min_result), c_void_p]
+        L.mm_probe_fma.argtypes = [dp]
         L.mm_batch_create.argtypes = [POINTER(c_void_p), c_int, POINTER(c_void_p)]
         L.mm_batch_destroy.argtypes = [c_void_p]
         L.mm_batch_sweep.argtypes = [c_void_p, POINTER(c_void_p), dp, c_int, c_int, POINTER(mm_min_opts), dp,
@@ -105,7 +106,7 @@ def lib():
         for name in ("mm_newell", "mm_newell_static", "mm_setup_geometry", "mm_destroy", "mm_heff", "mm_energy", "mm_minimize",
                      "mm_hysteresis_sweep", "mm_problem_info", "mm_kernel_times", "mm_energy_gradient",
                      "mm_hessian_vec", "mm_adjoint_dK", "mm_set_anisotropy", "mm_hysteresis_sweep_mixed", "mm_batch_create",
-                     "mm_batch_destroy", "mm_batch_sweep"):
+                     "mm_batch_destroy", "mm_batch_sweep", "mm_probe_fma"):
             getattr(L, name).restype = c_int
         _lib = L
     return _lib
@@ -329,6 +330,13 @@ def mm_kernel_times(prob: Problem, m, Hext, reps=20, stream=None) -> dict:
     _check(lib().mm_kernel_times(prob.handle, _ptr(m, prob.dtype, prob.shape, "m"), h[1], int(reps), ms, names,
                                  ctypes.byref(cnt), _stream(stream, m)), "mm_kernel_times")
     return {names[i].decode(): ms[i] for i in range(cnt.value)}
+
+
+def mm_probe_fma() -> dict:
+    """Measured FMA throughput of the current device (TFLOP/s): {"fp64": .., "fp32": ..}."""
+    out = (c_double * 2)()
+    _check(lib().mm_probe_fma(out), "mm_probe_fma")
+    return {"fp64": out[0], "fp32": out[1]}
 
 
 def mm_energy_gradient(prob: Problem, m, Hext, G_out, scale=1.0, stream=None):

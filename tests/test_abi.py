@@ -111,6 +111,10 @@ def test_newell_static_refuses_grids_past_its_buffer(L):
     lib = L.lib()
     big = L.make_grid(4096, 4096, 64, 1e-9, 1e-9, 1e-9)
     assert lib.mm_newell_static(ctypes.byref(big), ctypes.c_void_p(16), None) == L.MM_ERR_UNSUPPORTED
+    # nx + 1 would overflow a 32-bit int: the lattice count is taken in 64 bits
+    huge = L.make_grid(2**31 - 1, 1, 1, 1e-9, 1e-9, 1e-9)
+    assert lib.mm_newell_static(ctypes.byref(huge), ctypes.c_void_p(16), None) in (L.MM_ERR_UNSUPPORTED,
+                                                                                  L.MM_ERR_ARG)
     assert isinstance(L.mm_status_string(L.MM_ERR_UNSUPPORTED), str)
 
 

@@ -137,3 +137,83 @@ def test_loop_metrics_on_a_synthetic_loop():
     assert math.isclose(r["H_sw"], -3e-3 / om.MU0, rel_tol=1e-12)
     assert math.isclose(r["H_c"], -2.5e-3 / om.MU0, rel_tol=1e-12)
     assert r["M_r"] == 0.9
+
+
+def test_normalize_step_returns_unit_vectors_along_the_explicit_step():
+    """The renormalised explicit step, Eq. (projected_gradient_descent) in
+    descent orientation: unit length even for steps far too large for the
+    midpoint form, and parallel to m - tau g (a missing renormalisation, or
+    a step taken along +g, fails here)."""
+    m = inputs.random_unit_m((2, 3, 4), 21)
+    H = inputs.random_unit_m((2, 3, 4), 22) * 7e5
+    g = om.projected_gradient(m, H)
+    for tau in (1e-9, 1e-6, 3e-6, 1e-3):
+        m1 = om.normalize_step(m, g, tau)
+        assert np.max(np.abs(np.linalg.norm(m1, axis=0) - 1.0)) < 1e-15
+        v = m - tau * g
+        assert np.max(np.abs(np.cross(m1, v, axis=0))) < 1e-12 * np.max(np.linalg.norm(v, axis=0))
+        assert np.min(np.sum(m1 * v, axis=0)) > 0
+
+
+def _sw_cell(psi_deg):
+    Ms, K = 8e5, 2.0e5
+    prob = om.Problem(1, 1, 1, 4e-9, 4e-9, 4e-9, Ms=Ms, A=1.3e-11, K=K)
+    HK = 2 * K / (om.MU0 * Ms)
+    psi = math.radians(psi_deg)
+    return prob, HK, np.array([math.cos(psi), math.sin(psi), 0.0])
+
+
+def test_sweep_opens_the_stoner_wohlfarth_loop_on_both_branches():
+    """Section 4's driver on one cubic cell: descending then ascending
+    branch.  The loop only opens (switching at -h_sw going down and +h_sw
+    going up) if every field value starts from the previous magnetisation;
+    restarting each value from the initial state would switch back at once
+    on the ascending branch."""
+    psi_deg = 30.0
+    prob, HK, hdir = _sw_cell(psi_deg)
+    psi = math.radians(psi_deg)
+    hsw = (math.cos(psi) ** (2 / 3) + math.sin(psi) ** (2 / 3)) ** -1.5
+    step = 0.004
+    n = int(round(1.2 / step))
+    h_desc = [1.2 - step * i for i in range(2 * n + 1)]
+    h_asc = [-1.2 + step * i for i in range(1, 2 * n + 1)]
+    hs = np.array(h_desc + h_asc)
+    H_list = np.outer(hs * HK, hdir)
+    m0 = np.zeros((3, 1, 1, 1)); m0[0] = 1.0
+    mavg, res, mfin = om.sweep(prob, m0, H_list, om.Demag(prob, workers=1), tol=1e-10, max_iter=20000)
+    assert all(r.converged for r in res)
+    p = mavg @ hdir
+    nd = len(h_desc)
+    down = next(hs[i] for i in range(nd) if p[i] < 0)
+    up = next(hs[i] for i in range(nd, len(hs)) if p[i] > 0)
+    assert -hsw - step - 1e-9 < down <= -hsw + 1e-9
+    assert hsw - 1e-9 <= up < hsw + step + 1e-9
+    assert np.array_equal(mavg[-1], mfin.reshape(3, -1).mean(axis=1))
+
+
+def test_sweep_is_a_chain_of_fresh_minimisations():
+    """Per field value the driver runs one minimisation from the previous
+    result with the step-size history restarted (tau = tau0, k = 0); <m> is
+    the mean of that result.  Replaying the chain with independent calls
+    must give the same states, means and evaluation counts -- carrying tau
+    or the BB history across field values changes the counts."""
+    w = inputs.film_32x16x1()
+    prob = om.Problem(8, 4, 1, w.dx, w.dy, w.dz, Ms=w.Ms, A=w.A, K=w.K)
+    d = om.Demag(prob, workers=1)
+    H_list = inputs.sp1_sweep(20.0, 10.0)[:4]          # +20, +10, 0, -10 mT
+    m0 = inputs.tilted_uniform_m(prob.shape, 5)
+    mavg, res, mfin = om.sweep(prob, m0, H_list, d, tol=1e-6, max_iter=5000)
+    m = m0
+    for j, H in enumerate(H_list):
+        r = om.minimize(prob, m, H, d, tol=1e-6, max_iter=5000)
+        m = r.m
+        assert r.heff_evals == res[j].heff_evals and r.iters == res[j].iters
+        assert r.converged and res[j].converged
+        assert np.array_equal(mavg[j], m.reshape(3, -1).mean(axis=1))
+        assert mavg[j][0] != m[0, 0, 0, 0]      # a mean over distinct cells, not one cell
+    assert np.array_equal(m, mfin)
+    # the first step of every field value uses tau0: a sweep over one value
+    # equals a minimisation from the same state (no history to carry)
+    mavg1, res1, _ = om.sweep(prob, mfin, H_list[:1], d, tol=1e-6, max_iter=5000)
+    r1 = om.minimize(prob, mfin, H_list[0], d, tol=1e-6, max_iter=5000)
+    assert res1[0].heff_evals == r1.heff_evals
