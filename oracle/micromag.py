@@ -327,9 +327,17 @@ def normalize_step(m, g, tau):
     return v / np.linalg.norm(v, axis=0)
 
 
-def bb_tau(k, s, y, tau0):
+def bb_tau(k, s, y, tau0, rule="alternate", kappa=0.5):
     """Step size of Eq. (stepsize): tau^1 = sum s.s / sum s.y on odd k,
     tau^2 = sum s.y / sum y.y on even k (alternating, Section 2).
+
+    rule="adaptive": the paper names a "more elaborate switch" between the
+    two sizes without giving it.  Reading: the adaptive Barzilai-Borwein rule
+    of Zhou, Gao and Dai (Comput. Optim. Appl. 35 (2006) 69): take the short
+    size tau^2 when tau^2 / tau^1 = (s.y)^2 / ((s.s)(y.y)) < kappa, else the
+    long size tau^1, at every k >= 1.  The ratio is the squared cosine of
+    the angle between s and y; a small value means the last step met strongly
+    varying curvature, where the short size is the safer one.
 
     The paper is silent on non-positive curvature (sum s.y <= 0) and zero
     denominators.  Reading: use sqrt(sum s.s / sum y.y) (= |s|/|y|, the
@@ -341,7 +349,10 @@ def bb_tau(k, s, y, tau0):
     sy = np.float64(np.sum(s * y))
     yy = np.float64(np.sum(y * y))
     with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
-        tau = ss / sy if (k % 2 == 1) else sy / yy
+        if rule == "adaptive":
+            tau = sy / yy if (sy * sy) < kappa * (ss * yy) else ss / sy
+        else:
+            tau = ss / sy if (k % 2 == 1) else sy / yy
         if not (np.isfinite(tau) and tau > 0):
             tau = np.sqrt(ss / yy)
     if not (np.isfinite(tau) and tau > 0):
@@ -360,12 +371,13 @@ class MinResult:
 
 
 def minimize(prob: Problem, m0, Hext, demag: Demag, tol=1e-5, tau0=None, max_iter=100000,
-             step="cayley", record_taus=False):
+             step="cayley", record_taus=False, tau_rule="alternate", kappa=0.5):
     """Projected Barzilai-Borwein minimisation at one field value (Section 2).
 
     k counts steps within this minimisation.  Each pass: H = H_eff(m_k),
     g_k = m_k x (m_k x H); stop if max|m_k x H|/Ms < tol; stop unconverged
-    after max_iter steps; tau_k = tau0 for k = 0 else the BB value; step.
+    after max_iter steps; tau_k = tau0 for k = 0 else the BB value (``bb_tau``
+    with ``tau_rule``); step.
     """
     Ms = prob.Ms
     if tau0 is None:
@@ -385,7 +397,7 @@ def minimize(prob: Problem, m0, Hext, demag: Demag, tol=1e-5, tau0=None, max_ite
             return MinResult(m, k, evals, t, True, taus)
         if k >= max_iter:
             return MinResult(m, k, evals, t, False, taus)
-        tau = tau0 if k == 0 else bb_tau(k, m - m_prev, g - g_prev, tau0)
+        tau = tau0 if k == 0 else bb_tau(k, m - m_prev, g - g_prev, tau0, tau_rule, kappa)
         if record_taus:
             taus.append(tau)
         m_prev, g_prev = m, g
@@ -394,7 +406,7 @@ def minimize(prob: Problem, m0, Hext, demag: Demag, tol=1e-5, tau0=None, max_ite
 
 
 def sweep(prob: Problem, m0, H_list, demag: Demag, tol=1e-5, tau0=None, max_iter=100000,
-          step="cayley"):
+          step="cayley", tau_rule="alternate", kappa=0.5):
     """Hysteresis driver (Section 4): minimise once per field value, starting
     from the previous magnetisation; the BB history restarts at every field
     value.  Returns (mavg (n,3), list of MinResult without m, final m)."""
@@ -402,7 +414,8 @@ def sweep(prob: Problem, m0, H_list, demag: Demag, tol=1e-5, tau0=None, max_iter
     mavg = np.empty((len(H_list), 3))
     results = []
     for n, H in enumerate(H_list):
-        r = minimize(prob, m, H, demag, tol=tol, tau0=tau0, max_iter=max_iter, step=step)
+        r = minimize(prob, m, H, demag, tol=tol, tau0=tau0, max_iter=max_iter, step=step,
+                     tau_rule=tau_rule, kappa=kappa)
         m = r.m
         mavg[n] = m.reshape(3, -1).mean(axis=1)
         results.append(dataclasses.replace(r, m=None))

@@ -78,7 +78,7 @@ def test_bb_step_sizes_and_alternation():
     assert om.bb_tau(1, s, y * 0, 9.0) == 9.0
 
 
-def _sw_switching_field(psi_deg, step):
+def _sw_switching_field(psi_deg, step, tau_rule="alternate"):
     # One cubic cell: demag tensor is I/3, so H_d is parallel to m and exerts
     # no torque; without neighbours there is no exchange.  Uniaxial K along x.
     Ms, K = 8e5, 2.0e5
@@ -90,7 +90,7 @@ def _sw_switching_field(psi_deg, step):
     d = om.Demag(prob, workers=1)
     m = np.zeros((3, 1, 1, 1)); m[0] = 1.0
     for h in hs:
-        r = om.minimize(prob, m, h * HK * hdir, d, tol=1e-10, max_iter=20000)
+        r = om.minimize(prob, m, h * HK * hdir, d, tol=1e-10, max_iter=20000, tau_rule=tau_rule)
         assert r.converged
         m = r.m
         if float(np.sum(m[:, 0, 0, 0] * hdir)) < 0:
@@ -217,3 +217,57 @@ def test_sweep_is_a_chain_of_fresh_minimisations():
     mavg1, res1, _ = om.sweep(prob, mfin, H_list[:1], d, tol=1e-6, max_iter=5000)
     r1 = om.minimize(prob, mfin, H_list[0], d, tol=1e-6, max_iter=5000)
     assert res1[0].heff_evals == r1.heff_evals
+
+
+def _pair(a, b):
+    """s = (1, 0, 0), y = (a, b, 0) in one cell: s.s = 1, s.y = a, y.y = a^2 + b^2."""
+    s = np.zeros((3, 1, 1, 1)); s[0] = 1.0
+    y = np.zeros((3, 1, 1, 1)); y[0] = a; y[1] = b
+    return s, y
+
+
+def test_adaptive_switch_picks_by_the_angle_between_s_and_y():
+    """Adaptive BB (Zhou, Gao and Dai 2006): short size tau^2 when
+    (s.y)^2/((s.s)(y.y)) < kappa, else long size tau^1, whatever the parity of k."""
+    s, y = _pair(2.0, 1.0)            # cos^2 = 4/5: long size 1/2
+    for k in (1, 2, 3, 4):
+        assert om.bb_tau(k, s, y, 9.0, "adaptive", 0.5) == 0.5
+    s, y = _pair(1.0, 2.0)            # cos^2 = 1/5: short size 1/5
+    for k in (1, 2, 3, 4):
+        assert math.isclose(om.bb_tau(k, s, y, 9.0, "adaptive", 0.5), 0.2, rel_tol=1e-15)
+    assert om.bb_tau(1, s, y, 9.0, "adaptive", 0.1) == 1.0      # cos^2 = 0.2 >= 0.1: long size 1/1
+    s, y = _pair(-1.0, 1.0)           # negative curvature: |s|/|y| for both rules
+    for rule in ("alternate", "adaptive"):
+        assert math.isclose(om.bb_tau(2, s, y, 9.0, rule), 1 / math.sqrt(2), rel_tol=1e-15)
+
+
+@pytest.mark.parametrize("rule", ["alternate", "adaptive"])
+def test_bb_gradient_iteration_on_a_quadratic(rule):
+    """f(x) = x^T A x / 2, A = diag(1 .. 100): for a quadratic y = A s, so
+    both sizes are inverse Rayleigh quotients of A and lie in
+    [1/lambda_max, 1/lambda_min]; the BB gradient iteration converges
+    (Raydan, IMA J. Numer. Anal. 13 (1993) 321; the adaptive rule: Zhou, Gao
+    and Dai 2006)."""
+    lam = np.arange(1.0, 101.0).reshape(100, 1, 1, 1)
+    x = np.ones((100, 1, 1, 1))
+    g = lam * x
+    x_prev = g_prev = None
+    for k in range(400):
+        if np.linalg.norm(g) < 1e-10 * np.sqrt(np.sum(lam ** 2)):
+            break
+        tau = 1e-2 if k == 0 else om.bb_tau(k, x - x_prev, g - g_prev, 1e-2, rule)
+        assert 1 / 100 * (1 - 1e-12) <= tau <= 1.0 * (1 + 1e-12)
+        x_prev, g_prev = x, g
+        x = x - tau * g
+        g = lam * x
+    assert np.linalg.norm(g) < 1e-10 * np.sqrt(np.sum(lam ** 2)), (rule, k)
+
+
+@pytest.mark.parametrize("psi_deg", [1.0, 30.0])
+def test_stoner_wohlfarth_switching_with_the_adaptive_switch(psi_deg):
+    psi = math.radians(psi_deg)
+    hsw = (math.cos(psi) ** (2 / 3) + math.sin(psi) ** (2 / 3)) ** -1.5
+    step = 0.002
+    h = _sw_switching_field(psi_deg, step, tau_rule="adaptive")
+    assert h is not None
+    assert -hsw - step - 1e-9 < h <= -hsw + 1e-9
