@@ -492,6 +492,51 @@ def run_batch(args, ws, rank, local, dev):
     return 0
 
 
+def run_adjoint(args, dev):
+    """Implicit adjoint of the differentiation extension on the 128 x 64 x 2
+    film with per-cell K: relax at 0 mT from +x saturation (+50 mT first, as
+    the sweeps start), then time mm_adjoint_dK for d<m_x>/dK (CG to a relative
+    residual of 1e-11, one graph launch per solve) with CUDA events; W untimed
+    solves first.  Reports ms per solve and per CG iteration."""
+    import torch
+    from paper_1405_2728_gb300 import inputs, mm
+    w = inputs.film_128x64x2_random_K()
+    grid = mm.make_grid(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz)
+    prob = mm.mm_setup_geometry(grid, mm.make_material(w.Ms, w.A, 0.0, K_cell=w.K_cell), mm.MM_FP64)
+    m = torch.from_numpy(w.initial_m()).to(device=dev, dtype=torch.float64).contiguous()
+    mm.mm_minimize(prob, m, w.fields()[0], mm.make_opts(tol=1e-10, max_iter=400000))
+    st, r = mm.mm_minimize(prob, m, (0.0, 0.0, 0.0), mm.make_opts(tol=1e-14, max_iter=400000))
+    dJdm = torch.zeros_like(m)
+    dJdm[0] = 1.0 / w.ncells
+    out = torch.empty(m.shape[1:], dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        mm.mm_adjoint_dK(prob, m, (0.0, 0.0, 0.0), dJdm, out, tol=1e-11, max_iter=200000, stream=stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    its = []
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(args.steps):
+        sta, it, res = mm.mm_adjoint_dK(prob, m, (0.0, 0.0, 0.0), dJdm, out, tol=1e-11, max_iter=200000,
+                                        stream=stream)
+        its.append(it)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    kt = mm.mm_kernel_times(prob, m, (0.0, 0.0, 0.0), reps=30, stream=stream)
+    line = {"metric": "adjoint d<m_x>/dK solve time (128x64x2 film, per-cell K)", "value": ms, "unit": "ms/solve",
+            "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "cells": [w.nx, w.ny, w.nz], "cg_tol": 1e-11,
+                       "relaxed_to": "max|m x H|/Ms < 1e-14 at 0 mT"},
+            "cg_iterations": its, "ms_per_cg_iteration": ms / max(1, its[-1]), "status": int(sta),
+            "relaxation_status": int(st), "field_evaluation_ms": sum(kt.values()),
+            "gpu_launches_per_solve": int(6 + 8 * its[-1] + 1)}
+    print(json.dumps(line))
+    prob.close()
+    return 0
+
+
 def run_reference(args, ws, rank):
     """The oracle as it stands, on this host's cores: one minimisation of
     K iterations at the workload's first field value (tol 0, so it never
@@ -540,6 +585,8 @@ def main():
     ap.add_argument("--mixed-tol", type=float, default=3e-5)
     ap.add_argument("--workload", default="film_512x256x4")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time the implicit adjoint (differentiation extension) on the 128x64x2 film instead")
     ap.add_argument("--only", action="store_true",
                     help="measure only --precision (by default the line also carries the other precision)")
     ap.add_argument("--full-loop", action="store_true",
@@ -569,6 +616,8 @@ def main():
 
     if args.workload == "batch64":
         return run_batch(args, ws, rank, local, dev)
+    if args.adjoint:
+        return run_adjoint(args, dev)
     w = all_workloads(inputs)[args.workload]()
     if args.precision == "mixed":
         if not args.full_loop:

@@ -71,6 +71,7 @@ typedef enum {
 
 enum { MM_FP64 = 0, MM_FP32 = 1 };                   /* element type and arithmetic of the field path */
 enum { MM_STEP_CAYLEY = 0, MM_STEP_NORMALIZE = 1 };  /* update rule, see mm_min_opts */
+enum { MM_TAU_ALTERNATE = 0, MM_TAU_ADAPTIVE = 1 };  /* step-size rule, see mm_min_opts */
 
 /* Regular cuboid grid of nx*ny*nz cells of size dx*dy*dz (Section 3). */
 typedef struct {
@@ -135,8 +136,12 @@ MM_API int mm_newell_static(const mm_grid *grid, double *N_dev, void *stream);
  * power of two >= 2n-1, and >= 2 along x), times the admissible launch
  * shapes of the field kernels on this problem and keeps the fastest, and
  * captures the minimiser's CUDA graph.  precision = MM_FP64 or MM_FP32: element type of m/H and of the FFT
- * and stencil arithmetic; reductions (step sizes, energies, averages) are
- * always accumulated in double.
+ * and stencil arithmetic.  The reductions (step-size sums, energies,
+ * averages) are combined across CTAs in double and the step size is chosen in
+ * double.  Within a CTA the MM_FP64 path accumulates in double; the MM_FP32
+ * path adds every per-cell product exactly (an FMA-split product) into a
+ * compensated float pair (about 46 significant bits), which mm_min_inspect
+ * lets callers check against their own double reduction.
  * Two layouts of the y-z stage of the convolution.  Film layout (nz <= 4 and
  * the padded y-z plane of one x-frequency, about 3 * nz * 9/8 * Py complex
  * values, within 200 KiB of shared memory; e.g. 512 x 256 x 4 in FP64 or
@@ -187,16 +192,25 @@ MM_API int mm_energy(mm_problem *prob, const void *m, const double Hext[3], doub
  *           MM_STEP_NORMALIZE: m' = (m - tau g)/|m - tau g|, the explicit
  *           projected step Eq. (projected_gradient_descent) renormalised.
  * timeout_s wall-clock limit of the device loop in seconds (<= 0: none).
+ * tau_rule  MM_TAU_ALTERNATE: the alternation of Section 2;
+ *           MM_TAU_ADAPTIVE: the "more elaborate switch" the paper cites but
+ *           does not give, read as the adaptive Barzilai-Borwein rule of Zhou,
+ *           Gao and Dai (Comput. Optim. Appl. 35 (2006) 69): tau^2 when
+ *           tau^2/tau^1 = (s.y)^2/((s.s)(y.y)) < tau_kappa, else tau^1.
+ * tau_kappa threshold of the adaptive rule, in (0, 1]; <= 0 selects 0.5.
  * Step sizes: tau_0 = tau0; for k >= 1, with s = m_k - m_{k-1} and
  * y = g_k - g_{k-1} summed over all cells, tau^1 = s.s/s.y on odd k and
- * tau^2 = s.y/y.y on even k (Eq. stepsize, alternating); when that quotient
- * is not finite and positive, sqrt(s.s/y.y), else tau0. */
+ * tau^2 = s.y/y.y on even k (Eq. stepsize, alternating) or as tau_rule
+ * selects; when that quotient is not finite and positive, sqrt(s.s/y.y),
+ * else tau0. */
 typedef struct {
     double tol;
     double tau0;
     long max_iter;
     int step_kind;
     double timeout_s;
+    int tau_rule;
+    double tau_kappa;
 } mm_min_opts;
 
 /* Outcome of one minimisation. */
@@ -359,9 +373,33 @@ MM_API int mm_kernel_times(mm_problem *prob, const void *m, const double Hext[3]
                     const char **names, int *count, void *stream);
 
 /*
+ * mm_min_inspect -- instrumentation: the minimiser's device state after the
+ * last mm_minimize / mm_hysteresis_sweep on this problem (the last field
+ * value of a sweep).  out (host) receives the iterate index k of the last
+ * evaluation, the step size tau of the step that produced iterate k (tau0 at
+ * k = 0), the Barzilai-Borwein sums of Eq. (stepsize) at iterate k over all
+ * cells, s.s, s.y and y.y with s = m_k - m_{k-1} and y = g_k - g_{k-1}
+ * (zero at k = 0), max_i |m_i x H_i| / Ms at iterate k and the mm_status of
+ * that minimisation.  m_k, m_prev, g_k, g_prev (host or device, nullable,
+ * problem precision, [3][nz][ny][nx]) receive m_k, m_{k-1}, g_k = m_k x
+ * (m_k x H_k) and g_{k-1} as the kernels hold them (m_prev, g_prev
+ * meaningful for k >= 1).  Lets callers check the step-size sums against
+ * their own reduction of the same data.  Synchronises `stream`.
+ */
+typedef struct {
+    long k;
+    int status;
+    double tau;
+    double ss, sy, yy;
+    double max_torque;
+} mm_min_state;
+MM_API int mm_min_inspect(mm_problem *prob, mm_min_state *out, void *m_k, void *m_prev, void *g_k, void *g_prev,
+                          void *stream);
+
+/*
  * mm_probe_fma -- instrumentation: measured fused-multiply-add throughput of
  * the current device, tflops_out (host) [2] = FP64, FP32 in TFLOP/s (2 flops
- * per FMA), from independent FMA chains filling every SM, best of three ~5 ms
+ * per FMA), from independent FMA chains filling every SM, best of five ~5 ms
  * launches on the legacy default stream.  The double-precision field kernels
  * are bound by the FP64 units, so this is their roofline peak.  Allocates a
  * small buffer; synchronises the device.  (Instrumentation; not in the paper.)

@@ -86,6 +86,14 @@ bool mm_is_device_ptr(const void *ptr)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+bool mm_opts_ok(const mm_min_opts *o)
+{
+    return o && std::isfinite(o->tol) && o->tol >= 0 && std::isfinite(o->tau0) && o->max_iter >= 0 &&
+           (o->step_kind == MM_STEP_CAYLEY || o->step_kind == MM_STEP_NORMALIZE) && std::isfinite(o->timeout_s) &&
+           (o->tau_rule == MM_TAU_ALTERNATE || o->tau_rule == MM_TAU_ADAPTIVE) && std::isfinite(o->tau_kappa) &&
+           o->tau_kappa <= 1.0;
+}
+
 int mm_sm_count()
 {
     static int cached[256];
@@ -126,9 +134,10 @@ void free_problem(mm_problem *p)
     if (!p) return;
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->graph) cudaGraphDestroy(p->graph);
+    mm_adjoint_invalidate(p);
     void *bufs[] = {p->mbuf[0], p->mbuf[1], p->gbuf[0], p->gbuf[1], p->W, p->Nhat, p->tw_px, p->tw_py,
                     p->tw_pz, p->W2, p->Kc, p->uc, p->partials, p->st, p->Hext_dev, p->stage_in, p->stage_out,
-                    p->rec_dev, p->counter, p->adj[0], p->adj[1]};
+                    p->rec_dev, p->counter, p->adj[0], p->adj[1], p->adj_state, p->adj_partials};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (p->st_host) cudaFreeHost(p->st_host);
@@ -292,11 +301,7 @@ int mm_copy_user(void *dst, const void *src, size_t bytes, bool dst_dev, bool sr
 namespace {
 #define copy_user mm_copy_user
 
-bool opts_ok(const mm_min_opts *o)
-{
-    return o && std::isfinite(o->tol) && o->tol >= 0 && std::isfinite(o->tau0) && o->max_iter >= 0 &&
-           (o->step_kind == MM_STEP_CAYLEY || o->step_kind == MM_STEP_NORMALIZE) && std::isfinite(o->timeout_s);
-}
+bool opts_ok(const mm_min_opts *o) { return mm_opts_ok(o); }
 
 bool vec_ok(const double *h) { return h && std::isfinite(h[0]) && std::isfinite(h[1]) && std::isfinite(h[2]); }
 
@@ -601,9 +606,40 @@ extern "C" int mm_kernel_times(mm_problem *p, const void *m, const double Hext[3
     const size_t F = 3 * (size_t)p->g.N * p->esz;
     int rc;
     if ((rc = copy_user(p->mbuf[0], m, F, true, is_device_ptr(m), s))) return rc;
-    mm_min_opts o = {0.0, 0.0, 1L << 40, MM_STEP_CAYLEY, 0.0};
+    mm_min_opts o = {0.0, 0.0, 1L << 40, MM_STEP_CAYLEY, 0.0, MM_TAU_ALTERNATE, 0.0};
     if ((rc = mm_launch_init_state(p, Hext, &o, 1, s))) return rc;
     rc = mm_kernel_stage_times(p, reps, ms_out, names, count, s);
     CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
     return rc;
+}
+
+extern "C" int mm_min_inspect(mm_problem *p, mm_min_state *out, void *m_k, void *m_prev, void *g_k, void *g_prev,
+                              void *stream)
+{
+    NvtxRange nvtx_("mm_min_inspect");
+    if (!p || !out) return MM_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(MinState), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync");
+    CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    const MinState st = *p->st_host;
+    // buffers of iterate k: m in mbuf[base ^ (k & 1)], g in gbuf[k & 1]
+    const int cur = st.base ^ (int)(st.k & 1), gk = (int)(st.k & 1);
+    const size_t F = 3 * (size_t)p->g.N * p->esz;
+    void *dst[4] = {m_k, m_prev, g_k, g_prev};
+    void *src[4] = {p->mbuf[cur], p->mbuf[cur ^ 1], p->gbuf[gk], p->gbuf[gk ^ 1]};
+    for (int i = 0; i < 4; ++i) {
+        if (!dst[i]) continue;
+        const bool ddev = is_device_ptr(dst[i]);
+        int rc = copy_user(dst[i], src[i], F, ddev, true, s);
+        if (rc) return rc;
+    }
+    CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    out->k = st.k;
+    out->status = status_of(st.status == MMS_RUNNING ? MMS_CONVERGED : st.status);
+    out->tau = st.tau;
+    out->ss = st.bb[0];
+    out->sy = st.bb[1];
+    out->yy = st.bb[2];
+    out->max_torque = st.max_torque;
+    return MM_OK;
 }

@@ -97,8 +97,7 @@ extern "C" MM_API int mm_batch_sweep(mm_batch *b, void *const *m_list, const dou
                                      const mm_min_opts *opts, double *mavg, mm_min_result *per_step, void *stream)
 {
     if (!b || !m_list || !H_list || !mavg || n < 1 || start < 0 || start >= n || !opts) return MM_ERR_ARG;
-    if (!(std::isfinite(opts->tol) && opts->tol >= 0 && std::isfinite(opts->tau0) && opts->max_iter >= 0 &&
-          std::isfinite(opts->timeout_s) && (opts->step_kind == MM_STEP_CAYLEY || opts->step_kind == MM_STEP_NORMALIZE)))
+    if (!mm_opts_ok(opts))
         return MM_ERR_ARG;
     for (int j = 0; j < 3 * n; ++j)
         if (!std::isfinite(H_list[j])) return MM_ERR_ARG;

@@ -70,6 +70,9 @@ struct MinState {
     long launches;            // kernels launched by the loop body so far
     float Hextf[3];           // Hext and tau rounded once for the float kernels
     float tauf;
+    double bb[3];             // sums s.s, s.y, y.y over cells at iterate k (0 at k = 0)
+    int tau_rule;             // MM_TAU_ALTERNATE or MM_TAU_ADAPTIVE
+    double kappa;             // threshold of the adaptive rule
 };
 
 // Per-step record of a sweep
@@ -245,7 +248,18 @@ struct mm_problem {
     cudaGraphConditionalHandle cond;
     int graph_ready;
     int dev;
+    // device-side conjugate-gradient loop of the adjoint (built on first use)
+    cudaGraph_t adj_graph;
+    cudaGraphExec_t adj_exec;
+    cudaGraphConditionalHandle adj_cond;
+    void *adj_state;       // CgState (adjoint.cu)
+    double *adj_partials;  // per-CTA partial dot products
+    int adj_nblk;
 };
+
+// drop the adjoint's loop graph (it bakes in kernel parameters such as the
+// per-cell anisotropy pointer); rebuilt on the next mm_adjoint_dK
+void mm_adjoint_invalidate(mm_problem *p);
 
 // launchers implemented in heff.cu
 int mm_launch_min_body(mm_problem *p, cudaGraphConditionalHandle h, cudaStream_t s, int use_cond);
@@ -277,6 +291,8 @@ int mm_tensor_spectrum(mm_problem *p, const double *N_dev, cudaStream_t s);
 
 // helpers (api.cu)
 bool mm_is_device_ptr(const void *ptr);
+// options of a minimisation within range (finite tolerances, known rules)
+bool mm_opts_ok(const mm_min_opts *o);
 // streaming multiprocessors of the current device (queried once per device)
 int mm_sm_count();
 // grid of a grid-stride loop over n elements with `threads` per CTA: enough

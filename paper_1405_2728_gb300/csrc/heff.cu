@@ -26,9 +26,10 @@
 //             the step size tau^1 / tau^2 alternately (Eq. stepsize), applies
 //             the stop rule and sets the device-side loop condition.
 //
-// Sums are accumulated in double on the double path and in compensated
-// float pairs (TwoSum, Knuth) on the float path, and always combined across
-// CTAs in double.
+// Sums are accumulated in double on the double path.  On the float path each
+// per-cell product enters its sum exactly (TwoProduct with one FMA) and the
+// sums are compensated float pairs (TwoSum, Knuth), about 46 significant
+// bits; partial sums are always combined across CTAs in double.
 #include <cstdio>
 #include <cstring>
 
@@ -319,6 +320,7 @@ template <> struct Acc<double> {
     double v;
     __device__ __forceinline__ void zero() { v = 0.0; }
     __device__ __forceinline__ void add(double x) { v += x; }
+    __device__ __forceinline__ void add_prod(double a, double b) { v += a * b; }
     __device__ __forceinline__ void add(const Acc &o) { v += o.v; }
     __device__ __forceinline__ void maxv(double x) { v = fmax(v, x); }
     __device__ __forceinline__ void maxv(const Acc &o) { v = fmax(v, o.v); }
@@ -333,6 +335,16 @@ template <> struct Acc<float> {
         const float s = hi + x, bb = s - hi;
         lo += (hi - (s - bb)) + (x - bb);
         hi = s;
+    }
+    // a * b added exactly: the product is split into its rounded value and
+    // the rounding error (exact with one FMA: Dekker's TwoProduct in the form
+    // of Ogita, Rump and Oishi, SIAM J. Sci. Comput. 26 (2005) 1955)
+    __device__ __forceinline__ void add_prod(float a, float b)
+    {
+        const float p = __fmul_rn(a, b);
+        const float e = fmaf(a, b, -p);
+        add(p);
+        lo += e;
     }
     __device__ __forceinline__ void add(const Acc &o) { add(o.hi); lo += o.lo; }
     __device__ __forceinline__ void maxv(float x) { hi = fmaxf(hi, x); }
@@ -393,6 +405,9 @@ __device__ void finish_iteration(const Geom &g, double *partials, int nblk, MinS
     const long k = st->k;
     const double tmax = sqrt(tot[SL_T2]);
     st->max_torque = tmax / Ms;
+    st->bb[0] = k > 0 ? tot[SL_SS] : 0.0;
+    st->bb[1] = k > 0 ? tot[SL_SY] : 0.0;
+    st->bb[2] = k > 0 ? tot[SL_YY] : 0.0;
     st->energy[4] = cE * tot[SL_ET];
     st->evals = k + 1;
     st->launches += body_kernels;
@@ -414,7 +429,10 @@ __device__ void finish_iteration(const Geom &g, double *partials, int nblk, MinS
             tau = st->tau0;
         } else {
             const double ss = tot[SL_SS], sy = tot[SL_SY], yy = tot[SL_YY];
-            tau = (k & 1) ? ss / sy : sy / yy;
+            if (st->tau_rule == MM_TAU_ADAPTIVE)   // tau^2 when cos^2(s, y) < kappa, else tau^1
+                tau = (sy * sy < st->kappa * (ss * yy)) ? sy / yy : ss / sy;
+            else                                   // alternation: tau^1 on odd k, tau^2 on even k
+                tau = (k & 1) ? ss / sy : sy / yy;
             if (!(isfinite(tau) && tau > 0.0)) tau = sqrt(ss / yy);
             if (!(isfinite(tau) && tau > 0.0)) tau = st->tau0;
         }
@@ -587,10 +605,18 @@ __global__ void __launch_bounds__(768) k_xinv(Geom g, FieldPtrs<T> P, double hx0
         red[SL_MX].add(m0); red[SL_MY].add(m1); red[SL_MZ].add(m2);
         const T mhe = m0 * he0 + m1 * he1 + m2 * he2;
         if (MODE == MODE_ENERGY) {
-            red[SL_ED].add(m0 * d0 + m1 * d1 + m2 * d2);
-            red[SL_EEX].add(m0 * e0 + m1 * e1 + m2 * e2);
-            red[SL_EAN].add(Kv * ((T)1 - mu * mu));
-            red[SL_EZ].add(mhe);
+            if constexpr (sizeof(T) == 4) {
+                // float path: every per-cell product enters its sum exactly
+                red[SL_ED].add_prod(m0, d0); red[SL_ED].add_prod(m1, d1); red[SL_ED].add_prod(m2, d2);
+                red[SL_EEX].add_prod(m0, e0); red[SL_EEX].add_prod(m1, e1); red[SL_EEX].add_prod(m2, e2);
+                red[SL_EAN].add_prod(Kv, (T)1 - mu * mu);
+                red[SL_EZ].add_prod(m0, he0); red[SL_EZ].add_prod(m1, he1); red[SL_EZ].add_prod(m2, he2);
+            } else {
+                red[SL_ED].add(m0 * d0 + m1 * d1 + m2 * d2);
+                red[SL_EEX].add(m0 * e0 + m1 * e1 + m2 * e2);
+                red[SL_EAN].add(Kv * ((T)1 - mu * mu));
+                red[SL_EZ].add(mhe);
+            }
             continue;
         }
         // projected gradient g = m x (m x H) = (m.H) m - |m|^2 H (the triple
@@ -601,7 +627,14 @@ __global__ void __launch_bounds__(768) k_xinv(Geom g, FieldPtrs<T> P, double hx0
         const T g0 = mh * m0 - mm * H0, g1 = mh * m1 - mm * H1, g2 = mh * m2 - mm * H2;
         red[SL_T2].maxv(g0 * g0 + g1 * g1 + g2 * g2);  // |m x H|^2 = |g|^2 for |m| = 1
         // energy density / (mu0 Ms V): -m.H/2 - m.H_ext/2 + K/(mu0 Ms)
-        red[SL_ET].add((T)-0.5 * (mh + mhe) + kfac * Kv);
+        if constexpr (sizeof(T) == 4) {
+            const T h0 = (T)-0.5 * m0, h1 = (T)-0.5 * m1, h2 = (T)-0.5 * m2;  // exact halvings
+            red[SL_ET].add_prod(h0, H0); red[SL_ET].add_prod(h1, H1); red[SL_ET].add_prod(h2, H2);
+            red[SL_ET].add_prod(h0, he0); red[SL_ET].add_prod(h1, he1); red[SL_ET].add_prod(h2, he2);
+            red[SL_ET].add_prod(kfac, Kv);
+        } else {
+            red[SL_ET].add((T)-0.5 * (mh + mhe) + kfac * Kv);
+        }
         T *gout = (k & 1) ? P.gbuf[1] : P.gbuf[0];
         if (k > 0) {
             T p0, p1, p2, q0, q1, q2;
@@ -615,9 +648,17 @@ __global__ void __launch_bounds__(768) k_xinv(Geom g, FieldPtrs<T> P, double hx0
             }
             const T s0 = m0 - p0, s1 = m1 - p1, s2 = m2 - p2;
             const T y0v = g0 - q0, y1v = g1 - q1, y2v = g2 - q2;
-            red[SL_SS].add(s0 * s0 + s1 * s1 + s2 * s2);
-            red[SL_SY].add(s0 * y0v + s1 * y1v + s2 * y2v);
-            red[SL_YY].add(y0v * y0v + y1v * y1v + y2v * y2v);
+            if constexpr (sizeof(T) == 4) {
+                // float path: exact products, compensated sums (the step size
+                // needs s.y, a difference of nearly equal sums near convergence)
+                red[SL_SS].add_prod(s0, s0); red[SL_SS].add_prod(s1, s1); red[SL_SS].add_prod(s2, s2);
+                red[SL_SY].add_prod(s0, y0v); red[SL_SY].add_prod(s1, y1v); red[SL_SY].add_prod(s2, y2v);
+                red[SL_YY].add_prod(y0v, y0v); red[SL_YY].add_prod(y1v, y1v); red[SL_YY].add_prod(y2v, y2v);
+            } else {
+                red[SL_SS].add(s0 * s0 + s1 * s1 + s2 * s2);
+                red[SL_SY].add(s0 * y0v + s1 * y1v + s2 * y2v);
+                red[SL_YY].add(y0v * y0v + y1v * y1v + y2v * y2v);
+            }
         }
         gout[n] = g0; gout[N + n] = g1; gout[2 * N + n] = g2;
     }
@@ -664,7 +705,8 @@ __global__ void __launch_bounds__(768) k_xinv(Geom g, FieldPtrs<T> P, double hx0
 // small kernels
 // ---------------------------------------------------------------------------
 __global__ void k_init_state(MinState *st, double tau0, double tol_abs, double h0, double h1, double h2,
-                             long max_iter, int step_kind, unsigned long long timeout_ns, int reset_base)
+                             long max_iter, int step_kind, unsigned long long timeout_ns, int reset_base,
+                             int tau_rule, double kappa)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (reset_base) st->base = 0;
@@ -673,6 +715,7 @@ __global__ void k_init_state(MinState *st, double tau0, double tol_abs, double h
     st->Hext[0] = h0; st->Hext[1] = h1; st->Hext[2] = h2;
     st->Hextf[0] = (float)h0; st->Hextf[1] = (float)h1; st->Hextf[2] = (float)h2;
     st->max_iter = max_iter; st->step_kind = step_kind;
+    st->tau_rule = tau_rule; st->kappa = kappa;
     st->timeout_ns = timeout_ns; st->t_start_ns = 0;
     st->k = 0; st->tau = tau0; st->tauf = (float)tau0; st->status = MMS_RUNNING; st->evals = 0; st->launches = 1;
     st->max_torque = 0;
@@ -1077,8 +1120,9 @@ int mm_launch_init_state(mm_problem *p, const double Hext[3], const mm_min_opts 
 {
     double tau0 = o->tau0 > 0 ? o->tau0 : 1e-2 / p->g.Ms;
     unsigned long long to = o->timeout_s > 0 ? (unsigned long long)(o->timeout_s * 1e9) : 0ull;
+    const double kappa = o->tau_kappa > 0 ? o->tau_kappa : 0.5;
     k_init_state<<<1, 32, 0, s>>>(p->st, tau0, o->tol * p->g.Ms, Hext[0], Hext[1], Hext[2], o->max_iter,
-                                  o->step_kind, to, reset_base);
+                                  o->step_kind, to, reset_base, o->tau_rule, kappa);
     cudaError_t e = cudaGetLastError();
     if (e) { mm_set_cuda_error(e, "k_init_state"); return MM_ERR_CUDA; }
     return MM_OK;

@@ -55,11 +55,7 @@ int status_of_rec(int s)
     return MM_ERR_CUDA;
 }
 
-bool opts_valid(const mm_min_opts *o)
-{
-    return o && std::isfinite(o->tol) && o->tol >= 0 && std::isfinite(o->tau0) && o->max_iter >= 0 &&
-           std::isfinite(o->timeout_s) && (o->step_kind == MM_STEP_CAYLEY || o->step_kind == MM_STEP_NORMALIZE);
-}
+bool opts_valid(const mm_min_opts *o) { return mm_opts_ok(o); }
 
 int ensure_records(mm_problem *p, int n)
 {

@@ -11,7 +11,7 @@
 namespace {
 
 constexpr int PROBE_THREADS = 256;
-constexpr int NCH = 8;
+constexpr int NCH = 16;
 
 template <typename T>
 __global__ void __launch_bounds__(PROBE_THREADS) k_fma_chains(int iters, T a, T b, T *sink)
@@ -19,6 +19,7 @@ __global__ void __launch_bounds__(PROBE_THREADS) k_fma_chains(int iters, T a, T 
     T x[NCH];
 #pragma unroll
     for (int c = 0; c < NCH; ++c) x[c] = (T)(threadIdx.x + c) * (T)1e-3;
+#pragma unroll 4
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
         for (int c = 0; c < NCH; ++c) x[c] = fma(x[c], a, b);
@@ -39,7 +40,7 @@ int time_chains(int blocks, int iters, T *sink, double *tflops)
     const T fa = (T)0.9999999, fb = (T)1e-7;
     float best = 1e30f;
     cudaError_t e = cudaSuccess;
-    for (int r = 0; r < 4 && !e; ++r) {  // first launch warms the clocks; best of the rest
+    for (int r = 0; r < 6 && !e; ++r) {  // first launch warms the clocks; best of the rest
         cudaEventRecord(a, 0);
         k_fma_chains<T><<<blocks, PROBE_THREADS>>>(iters, fa, fb, sink);
         cudaEventRecord(b, 0);
@@ -67,8 +68,8 @@ extern "C" MM_API int mm_probe_fma(double tflops_out[2])
     if (e) { mm_set_cuda_error(e, "cudaMalloc"); return MM_ERR_OOM; }
     // about 5 ms per launch at the nominal rates (2 FP64 and 128 FP32 FMA
     // per SM per clock)
-    int rc = time_chains<double>(blocks, 1250, sink, &tflops_out[0]);
-    if (rc == MM_OK) rc = time_chains<float>(blocks, 1250 * 64, (float *)sink, &tflops_out[1]);
+    int rc = time_chains<double>(blocks, 624, sink, &tflops_out[0]);
+    if (rc == MM_OK) rc = time_chains<float>(blocks, 624 * 64, (float *)sink, &tflops_out[1]);
     cudaFree(sink);
     return rc;
 }

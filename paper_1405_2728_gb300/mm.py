@@ -23,6 +23,7 @@ MM_OK, MM_ERR_ARG, MM_ERR_OOM, MM_ERR_CUDA = 0, -1, -2, -3
 MM_ERR_NOT_CONVERGED, MM_ERR_NONFINITE, MM_ERR_TIMEOUT, MM_ERR_UNSUPPORTED = -4, -5, -6, -7
 MM_FP64, MM_FP32 = 0, 1
 MM_STEP_CAYLEY, MM_STEP_NORMALIZE = 0, 1
+MM_TAU_ALTERNATE, MM_TAU_ADAPTIVE = 0, 1
 
 
 class mm_grid(ctypes.Structure):
@@ -36,7 +37,7 @@ class mm_material(ctypes.Structure):
 
 class mm_min_opts(ctypes.Structure):
     _fields_ = [("tol", c_double), ("tau0", c_double), ("max_iter", c_long), ("step_kind", c_int),
-                ("timeout_s", c_double)]
+                ("timeout_s", c_double), ("tau_rule", c_int), ("tau_kappa", c_double)]
 
 
 class mm_min_result(ctypes.Structure):
@@ -53,6 +54,14 @@ class mm_info(ctypes.Structure):
                 ("spectrum_bytes", c_long), ("tensor_bytes", c_long), ("x_tile_rows", c_int),
                 ("yz_batch_rows", c_int), ("bulk_layout", c_int),
                 ("x_fwd_tile_rows", c_int)]
+
+
+class mm_min_state(ctypes.Structure):
+    _fields_ = [("k", c_long), ("status", c_int), ("tau", c_double), ("ss", c_double), ("sy", c_double),
+                ("yy", c_double), ("max_torque", c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class MMError(RuntimeError):
@@ -96,6 +105,8 @@ def lib():
                                                 POINTER(mm_min_opts), POINTER(mm_min_opts), dp,
                                                 POINTER(mm_min_result), POINTER(mm_min_result), c_void_p]
         L.mm_probe_fma.argtypes = [dp]
+        L.mm_min_inspect.argtypes = [c_void_p, POINTER(mm_min_state), c_void_p, c_void_p, c_void_p, c_void_p,
+                                     c_void_p]
         L.mm_batch_create.argtypes = [POINTER(c_void_p), c_int, POINTER(c_void_p)]
         L.mm_batch_destroy.argtypes = [c_void_p]
         L.mm_batch_sweep.argtypes = [c_void_p, POINTER(c_void_p), dp, c_int, c_int, POINTER(mm_min_opts), dp,
@@ -106,7 +117,7 @@ def lib():
         for name in ("mm_newell", "mm_newell_static", "mm_setup_geometry", "mm_destroy", "mm_heff", "mm_energy", "mm_minimize",
                      "mm_hysteresis_sweep", "mm_problem_info", "mm_kernel_times", "mm_energy_gradient",
                      "mm_hessian_vec", "mm_adjoint_dK", "mm_set_anisotropy", "mm_hysteresis_sweep_mixed", "mm_batch_create",
-                     "mm_batch_destroy", "mm_batch_sweep", "mm_probe_fma"):
+                     "mm_batch_destroy", "mm_batch_sweep", "mm_probe_fma", "mm_min_inspect"):
             getattr(L, name).restype = c_int
         _lib = L
     return _lib
@@ -216,8 +227,10 @@ def make_material(Ms, A, K=0.0, u=(1.0, 0.0, 0.0), K_cell=None, u_cell=None) -> 
     return mat
 
 
-def make_opts(tol=1e-5, tau0=0.0, max_iter=100000, step_kind=MM_STEP_CAYLEY, timeout_s=0.0) -> mm_min_opts:
-    return mm_min_opts(float(tol), float(tau0), int(max_iter), int(step_kind), float(timeout_s))
+def make_opts(tol=1e-5, tau0=0.0, max_iter=100000, step_kind=MM_STEP_CAYLEY, timeout_s=0.0,
+              tau_rule=MM_TAU_ALTERNATE, tau_kappa=0.0) -> mm_min_opts:
+    return mm_min_opts(float(tol), float(tau0), int(max_iter), int(step_kind), float(timeout_s), int(tau_rule),
+                       float(tau_kappa))
 
 
 def mm_newell(grid: mm_grid, N_out, stream=None):
@@ -330,6 +343,17 @@ def mm_kernel_times(prob: Problem, m, Hext, reps=20, stream=None) -> dict:
     _check(lib().mm_kernel_times(prob.handle, _ptr(m, prob.dtype, prob.shape, "m"), h[1], int(reps), ms, names,
                                  ctypes.byref(cnt), _stream(stream, m)), "mm_kernel_times")
     return {names[i].decode(): ms[i] for i in range(cnt.value)}
+
+
+def mm_min_inspect(prob: Problem, m_k=None, m_prev=None, g_k=None, g_prev=None, stream=None) -> dict:
+    """State of the last minimisation (iterate index, step size, BB sums, torque,
+    status); optional arrays receive m_k, m_{k-1}, g_k, g_{k-1}."""
+    out = mm_min_state()
+    bufs = [None if a is None else _ptr(a, prob.dtype, prob.shape, "buffer") for a in (m_k, m_prev, g_k, g_prev)]
+    _check(lib().mm_min_inspect(prob.handle, ctypes.byref(out), *bufs,
+                                _stream(stream, *[a for a in (m_k, m_prev, g_k, g_prev) if a is not None])),
+           "mm_min_inspect")
+    return out.as_dict()
 
 
 def mm_probe_fma() -> dict:

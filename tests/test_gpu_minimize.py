@@ -113,3 +113,37 @@ def test_sweep_resume_equals_single_sweep(mmlib):
     _, mavg2, _ = mmlib.mm_hysteresis_sweep(prob, m2, F, start=17, opts=mmlib.make_opts(tol=w.tol), mavg=mavg2)
     assert np.array_equal(mavg1, mavg2)
     assert torch.equal(m1, m2)
+
+
+@pytest.mark.parametrize("step", [0, 1])
+def test_adaptive_step_size_rule_follows_the_oracle(mmlib, step):
+    """The adaptive switch between the two Barzilai-Borwein sizes (tau_rule
+    MM_TAU_ADAPTIVE) against the oracle's bb_tau(rule="adaptive")."""
+    w, prob, oprob = small_film(mmlib)
+    m0 = inputs.random_unit_m(oprob.shape, 23)
+    H = w.fields()[40]
+    m = dev(m0)
+    opts = mmlib.make_opts(tol=0.0, max_iter=25, step_kind=step, tau_rule=mmlib.MM_TAU_ADAPTIVE, tau_kappa=0.5)
+    st, r = mmlib.mm_minimize(prob, m, H, opts)
+    assert st == mmlib.MM_ERR_NOT_CONVERGED and r.iters == 25
+    ref = om.minimize(oprob, m0, H, om.Demag(oprob), tol=0.0, max_iter=25,
+                      step="cayley" if step == 0 else "normalize", tau_rule="adaptive", kappa=0.5)
+    assert rel_l2(m.cpu().numpy(), ref.m) <= 1e-8
+    # the rules differ: the adaptive trajectory is not the alternating one
+    alt = om.minimize(oprob, m0, H, om.Demag(oprob), tol=0.0, max_iter=25,
+                      step="cayley" if step == 0 else "normalize")
+    assert rel_l2(alt.m, ref.m) > 1e-6
+
+
+def test_adaptive_rule_converged_loop_32x16x1_matches_oracle(mmlib):
+    w, prob, oprob = small_film(mmlib)
+    F = w.fields()
+    mavg_ref, res_ref, _ = om.sweep(oprob, w.initial_m(), F, om.Demag(oprob), tol=w.tol, tau_rule="adaptive")
+    m = dev(w.initial_m())
+    st, mavg, res = mmlib.mm_hysteresis_sweep(prob, m, F, opts=mmlib.make_opts(tol=w.tol,
+                                                                               tau_rule=mmlib.MM_TAU_ADAPTIVE))
+    assert st == mmlib.MM_OK and all(r.converged for r in res)
+    a, b = om.loop_metrics(F, mavg), om.loop_metrics(F, mavg_ref)
+    step = np.linalg.norm(F[0] - F[1])
+    assert abs(a["H_sw"] - b["H_sw"]) <= step * (1 + 1e-9)
+    assert abs(a["M_r"] - b["M_r"]) <= 1e-3
