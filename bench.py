@@ -38,6 +38,9 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # nominal FMA lanes per SM per clock (the measured rates come from mm_probe_fma)
 FP64_FMA_PER_SM_CLK = 2
 FP32_FMA_PER_SM_CLK = 128
+DW_ADD_INSTRUCTIONS = 11      # FP32 instructions of one double-word (float pair) addition
+PRECISIONS = {"fp64": 0, "fp32": 1, "f32x2": 2}   # mm.MM_FP64, mm.MM_FP32, mm.MM_F32X2
+DTYPE_LABEL = {"fp64": "f64", "fp32": "f32", "f32x2": "f64 fields, f32x2 (double-word) FFT and convolution"}
 
 
 def dist_env():
@@ -202,7 +205,7 @@ def survey_flops(info):
     return out
 
 
-KERNEL_SOURCES = ("common.cuh", "fft.cuh", "heff.cu")  # what the three film field kernels compile from
+KERNEL_SOURCES = ("common.cuh", "fft.cuh", "field_kernels.cuh", "heff.cu")  # what the film field kernels compile from
 
 
 def kernel_source_hash():
@@ -334,7 +337,7 @@ def run_full_loop(args, w, prob, m, F, opts, stream, tdt, esz, info, dev):
     hhat = hhat / np.linalg.norm(hhat)
     line = {"metric": METRIC, "value": evals / sec, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if esz == 8 else "f32", "data": "synthetic",
+            "dtype": DTYPE_LABEL[args.precision], "data": "synthetic",
             "config": {"workload": w.name, "cells": [w.nx, w.ny, w.nz], "precision": args.precision,
                        "step": f"one whole loop: {len(F)} field values minimised to tol {w.tol:g}"},
             "loop_time_s": sec, "loop_evals": int(evals),
@@ -361,7 +364,7 @@ def run_mixed_loop(args, w, dev):
     grid = mm.make_grid(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz)
     mat = mm.make_material(w.Ms, w.A, w.K, K_cell=w.K_cell, u_cell=w.u_cell)
     lo = mm.mm_setup_geometry(grid, mat, mm.MM_FP32)
-    hi = mm.mm_setup_geometry(grid, mat, mm.MM_FP64)
+    hi = mm.mm_setup_geometry(grid, mat, PRECISIONS[args.mixed_hi])
     F = w.fields()
     o_lo = mm.make_opts(tol=args.mixed_tol, max_iter=20000)
     o_hi = mm.make_opts(tol=w.tol, max_iter=args.max_iter)
@@ -390,10 +393,10 @@ def run_mixed_loop(args, w, dev):
     sw = [float(h[i]) for i in range(1, nd) if p[i] < 0]
     line = {"metric": METRIC, "value": (ev_lo + ev_hi) / sec, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64", "data": "synthetic",
+            "dtype": "f32+" + DTYPE_LABEL[args.mixed_hi], "data": "synthetic",
             "config": {"workload": w.name, "cells": [w.nx, w.ny, w.nz], "precision": "mixed",
                        "step": f"one whole loop: {len(F)} field values, FP32 to tol {args.mixed_tol:g} "
-                               f"then FP64 to tol {w.tol:g}"},
+                               f"then {args.mixed_hi} to tol {w.tol:g}"},
             "loop_time_s": sec, "loop_evals_fp32": int(ev_lo), "loop_evals_fp64": int(ev_hi),
             "converged_field_values": int(sum(r.converged for r in rh)), "field_values": len(F),
             "status": int(st), "H_sw_mT": sw[0] if sw else None,
@@ -412,9 +415,11 @@ def all_workloads(inputs):
 def run_batch(args, ws, rank, local, dev):
     """64 films of uneven size (inputs.batch_films), FP64, each with its own
     +-50 mT sweep in 2 mT steps.  A step is one field value for every film:
-    all 64 minimisations through mm_batch_sweep (one stream per film, films
-    running concurrently), then the same field value film by film with
-    mm_hysteresis_sweep for the sequential comparison."""
+    K field values for all 64 films in one mm_batch_sweep call (one graph
+    launch whose loop runs one grouped launch per kernel stage over every film
+    still running, each film walking its own field values), then the same K
+    field values film by film with mm_hysteresis_sweep for the sequential
+    comparison.  The L2 is flushed before each of the two timed calls."""
     import torch
     from paper_1405_2728_gb300 import inputs, mm
     films = inputs.batch_films(64)
@@ -430,43 +435,42 @@ def run_batch(args, ws, rank, local, dev):
     ms_s = [m.clone() for m in ms_b]
     flush = torch.empty(int(256 * 2**20) // 4, dtype=torch.float32, device=dev)
 
-    def batch_step(i):
-        st, _, res = mm.mm_batch_sweep(batch, ms_b, F[: i + 1], start=i, opts=opts, stream=stream)
-        return sum(r[i].heff_evals for r in res), sum(r[i].kernel_launches for r in res)
+    def batch_sweep(i0, k):
+        """field values i0 .. i0+k-1 for all films in one mm_batch_sweep call
+        (one graph launch: every film walks its own field values)"""
+        st, _, res = mm.mm_batch_sweep(batch, ms_b, F[: i0 + k], start=i0, opts=opts, stream=stream)
+        ev = sum(r[j].heff_evals for r in res for j in range(i0, i0 + k))
+        # per loop iteration three grouped stage kernels and the advance
+        # kernel; iterations = the largest total of evaluations of one film
+        iters = max(sum(r[j].heff_evals for j in range(i0, i0 + k)) for r in res)
+        return ev, 1 + 4 * iters
 
-    def seq_step(i):
+    def seq_sweep(i0, k):
         ev = 0
         for p, m in zip(probs, ms_s):
-            st, _, res = mm.mm_hysteresis_sweep(p, m, F[: i + 1], start=i, opts=opts, stream=stream)
-            ev += res[i].heff_evals
+            st, _, res = mm.mm_hysteresis_sweep(p, m, F[: i0 + k], start=i0, opts=opts, stream=stream)
+            ev += sum(res[j].heff_evals for j in range(i0, i0 + k))
         return ev
 
-    for i in range(args.warmup):
-        batch_step(i)
-        seq_step(i)
+    batch_sweep(0, args.warmup)
+    seq_sweep(0, args.warmup)
     torch.cuda.synchronize()
     K = args.steps
     sampler = ClockSampler(local)
-    ev_b = ev_s = launches = 0
-    t_b = t_s = 0.0
     with sampler:
-        for j in range(K):
-            i = (args.warmup + j) % len(F)
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            e, l = batch_step(i)
-            b.record(stream)
-            torch.cuda.synchronize()
-            t_b += a.elapsed_time(b)
-            ev_b += e
-            launches += l
-            flush.zero_()
-            a.record(stream)
-            ev_s += seq_step(i)
-            b.record(stream)
-            torch.cuda.synchronize()
-            t_s += a.elapsed_time(b)
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ev_b, launches = batch_sweep(args.warmup, K)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_b = a.elapsed_time(b)
+        flush.zero_()
+        a.record(stream)
+        ev_s = seq_sweep(args.warmup, K)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_s = a.elapsed_time(b)
     clocks = sampler.summary()
     if rank != 0:
         return 0
@@ -477,8 +481,12 @@ def run_batch(args, ws, rank, local, dev):
         "ms_per_step": t_b / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == mm.MM_FP64 else "f32", "data": "synthetic",
         "config": {"workload": "batch64_films", "films": len(films), "cells_min_max_sum": [min(cells), max(cells), sum(cells)],
-                   "precision": args.precision, "step": "one field value of the +-50 mT / 2 mT sweep for all 64 films, tol 1e-5",
-                   "l2": "flushed between steps (256 MiB write)", "parallelism": "one stream per film"},
+                   "precision": args.precision,
+                   "step": "one field value of the +-50 mT / 2 mT sweep for all 64 films, tol 1e-5; the K timed "
+                           "steps are one mm_batch_sweep call",
+                   "l2": "flushed before each timed call (256 MiB write)",
+                   "parallelism": "one graph launch per sweep call; one grouped launch per kernel stage over the "
+                                  "films still running, each film at its own field value"},
         "sequential": {"value": ev_s / (t_s / 1e3), "unit": UNIT, "ms_per_step": t_s / K,
                        "evals_per_step": ev_s / K, "speedup_batched": t_s / t_b},
         "evals_per_step": ev_b / K,
@@ -580,9 +588,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed"],
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "f32x2", "mixed"],
                     help="mixed: FP32 minimisation to --mixed-tol, then FP64 to the final tolerance (with --full-loop)")
     ap.add_argument("--mixed-tol", type=float, default=3e-5)
+    ap.add_argument("--mixed-hi", default="fp64", choices=["fp64", "f32x2"],
+                    help="precision of the second (final-tolerance) phase of --precision mixed")
     ap.add_argument("--workload", default="film_512x256x4")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--adjoint", action="store_true",
@@ -623,9 +633,9 @@ def main():
         if not args.full_loop:
             ap.error("--precision mixed is measured as a whole loop: add --full-loop")
         return run_mixed_loop(args, w, dev)
-    prec = mm.MM_FP64 if args.precision == "fp64" else mm.MM_FP32
-    tdt = torch.float64 if prec == mm.MM_FP64 else torch.float32
-    esz = 8 if prec == mm.MM_FP64 else 4
+    prec = PRECISIONS[args.precision]
+    tdt = torch.float32 if prec == mm.MM_FP32 else torch.float64
+    esz = 4 if prec == mm.MM_FP32 else 8
     grid = mm.make_grid(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz)
     prob = mm.mm_setup_geometry(grid, mm.make_material(w.Ms, w.A, w.K, K_cell=w.K_cell, u_cell=w.u_cell), prec)
     info = mm.mm_problem_info(prob)
@@ -712,14 +722,26 @@ def main():
         event times over 30 repetitions on the launching stream."""
         kt = mm.mm_kernel_times(p, buf, F[at_field], reps=30, stream=stream)
         inf = mm.mm_problem_info(p)
-        e = 8 if pname == "fp64" else 4
+        e = 4 if pname == "fp32" else 8
         model = algorithmic_model(inf, e)
         sflops = survey_flops(inf)
         dom = max(kt, key=kt.get)
         sec = kt[dom] * 1e-3
         gbs = model[dom]["bytes"] / sec / 1e9
         hbm = peaks.get("hbm_gbs")
-        if pname == "fp64":
+        if pname == "f32x2":
+            # double-word arithmetic on the FP32 pipes: one double-word add
+            # (the bulk of an FFT) takes 11 FP32 instructions, a product 6
+            peak = fma["fp32"] / 2 / DW_ADD_INSTRUCTIONS
+            ach = sflops[dom] / sec / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s (double-word)",
+                    "frac": ach / peak,
+                    "peak_source": f"measured FP32 FMA throughput {fma['fp32']:.1f} TFLOP/s = {fma['fp32'] / 2:.1f} T "
+                                   f"instructions/s, / {DW_ADD_INSTRUCTIONS} instructions per double-word add",
+                    "flop_model": "workload reference model (2.5/5 L log2 L per real/complex transform, 36 per "
+                                  "frequency, 200 per cell)",
+                    "vs_fp64_fma_peak": ach / fma["fp64"]}
+        elif pname == "fp64":
             derived = n_sm * FP64_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12
             peak = fma["fp64"]
             ach = sflops[dom] / sec / 1e12
@@ -750,7 +772,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec == mm.MM_FP64 else "f32", "data": "synthetic",
+        "dtype": DTYPE_LABEL[args.precision], "data": "synthetic",
         "config": {"workload": w.name, "cells": [w.nx, w.ny, w.nz], "padded": [info["px"], info["py"], info["pz"]],
                    "precision": args.precision,
                    "step": f"one field value of the {len(F)}-value sweep minimised to tol {w.tol:g}"
@@ -769,10 +791,10 @@ def main():
         "fma_peaks_tflops": fma,
     }
     # the other precision of the metric on the same workload and field values
-    other = [] if args.only else [q for q in ("fp64", "fp32") if q != args.precision]
+    other = [] if args.only else [q for q in ("fp64", "fp32", "f32x2") if q != args.precision]
     for q in other:
-        qprec = mm.MM_FP64 if q == "fp64" else mm.MM_FP32
-        qdt = torch.float64 if q == "fp64" else torch.float32
+        qprec = PRECISIONS[q]
+        qdt = torch.float32 if q == "fp32" else torch.float64
         qp = mm.mm_setup_geometry(grid, mm.make_material(w.Ms, w.A, w.K, K_cell=w.K_cell, u_cell=w.u_cell), qprec)
         qm = torch.from_numpy(w.initial_m()).to(device=dev, dtype=qdt).contiguous()
         for i in range(args.warmup):
@@ -782,7 +804,7 @@ def main():
             qms, qev, qla, qst = timed_steps(qp, qm, args.warmup, K)
         qroof, _ = roofline(qp, q, qm, args.warmup)
         qinfo = mm.mm_problem_info(qp)
-        line[q] = {"value": qev / (qms / 1e3), "unit": UNIT, "dtype": "f64" if q == "fp64" else "f32",
+        line[q] = {"value": qev / (qms / 1e3), "unit": UNIT, "dtype": DTYPE_LABEL[q],
                    "ms_per_step": qms / K, "evals_per_step": qev / K, "statuses": qst, "gpu_launches": int(qla),
                    "loop_time_s_est": len(F) * (qms / K) / 1e3, "roofline": qroof, "clocks": qsampler.summary(),
                    "launch_shape": {k: qinfo[k] for k in ("x_fwd_tile_rows", "x_tile_rows", "yz_batch_rows")}}

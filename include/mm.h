@@ -69,7 +69,12 @@ typedef enum {
     MM_ERR_UNSUPPORTED = -7     /* valid but outside what this build supports (see mm_setup_geometry) */
 } mm_status;
 
-enum { MM_FP64 = 0, MM_FP32 = 1 };                   /* element type and arithmetic of the field path */
+/* Element type and arithmetic of the field path.  MM_F32X2 (an extension):
+ * fields in double as for MM_FP64, the FFTs and the demagnetisation
+ * convolution in double-float arithmetic (pairs of floats, about 48
+ * significant bits, run on the FP32 pipes), the local terms, the step and
+ * the reductions in double; film-layout grids only (see mm_setup_geometry). */
+enum { MM_FP64 = 0, MM_FP32 = 1, MM_F32X2 = 2 };
 enum { MM_STEP_CAYLEY = 0, MM_STEP_NORMALIZE = 1 };  /* update rule, see mm_min_opts */
 enum { MM_TAU_ALTERNATE = 0, MM_TAU_ADAPTIVE = 1 };  /* step-size rule, see mm_min_opts */
 
@@ -323,14 +328,29 @@ MM_API int mm_hysteresis_sweep_mixed(mm_problem *lo, mm_problem *hi, void *m, co
  * Batched sweeps (an extension; the paper sweeps one sample).  A batch
  * references existing problems (of any sizes and precisions; the caller keeps
  * owning them and must not destroy them while the batch exists) and runs
- * their hysteresis sweeps together.  Each problem keeps its own device-side
- * minimiser loop (its CUDA graph, with the launch shapes its setup autotuner
- * chose) and gets a stream of its own; for every field value the batch issues
- * every problem's minimisation on its stream, so the problems run
- * concurrently on the GPU.  mm_batch_create returns MM_ERR_ARG for a null
- * or repeated problem (one problem's buffers cannot serve two streams) and for
- * one whose setup did not finish; the batch owns one stream and one event per
- * problem, released by mm_batch_destroy.
+ * their hysteresis sweeps together.
+ * Grouped path (every problem film-layout, MM_FP64 or MM_FP32): one sweep
+ * call is ONE graph launch.  Its device-side loop runs one minimiser
+ * iteration of every problem still running per pass -- one grouped kernel
+ * launch per stage and precision over the work items of all those problems --
+ * and each problem moves on to its next field value as soon as its
+ * minimisation at the current one ends, so problems advance at their own
+ * pace.  Each work item runs the problem's own kernel body with the
+ * problem's own tile, partial sums and state, so every problem's results
+ * equal its own mm_hysteresis_sweep bit for bit.  mm_batch_create gives all
+ * members of a precision the tile thread counts of the largest member (one
+ * CTA shape per grouped launch): it may change the launch shapes of smaller
+ * members, and recaptures their minimiser graphs, so their later single
+ * sweeps use the same shapes.
+ * Stream path (any bulk-layout or MM_F32X2 member): each problem keeps its own
+ * device-side loop and gets a stream of its own; for every field value the
+ * batch issues every problem's minimisation on its stream, so the problems
+ * run concurrently on the GPU.
+ * mm_batch_create returns MM_ERR_ARG for a null or repeated problem (one
+ * problem's buffers cannot serve two work lists) and for one whose setup did
+ * not finish; the batch owns its tables, graph or streams, released by
+ * mm_batch_destroy.  The caller must not destroy a member while the batch
+ * exists.
  *
  * mm_batch_sweep: as mm_hysteresis_sweep for every problem i with the same
  * field list H_list[n][3] (host, A/m): m_list[i] (host or device, in/out) is

@@ -365,7 +365,7 @@ extern "C" MM_API int mm_hessian_vec(mm_problem *p, const void *m, const double 
                                      void *stream)
 {
     if (!p || !m || !v || !Av || !vec3_ok(Hext)) return MM_ERR_ARG;
-    return p->precision == MM_FP64 ? hvp_t<double>(p, m, Hext, v, Av, (cudaStream_t)stream)
+    return mm_double_fields(p) ? hvp_t<double>(p, m, Hext, v, Av, (cudaStream_t)stream)
                                    : hvp_t<float>(p, m, Hext, v, Av, (cudaStream_t)stream);
 }
 
@@ -374,7 +374,7 @@ extern "C" MM_API int mm_adjoint_dK(mm_problem *p, const void *m, const double H
                                     void *stream)
 {
     if (!p || !m || !dJdm || !dJdK || !vec3_ok(Hext) || !(tol > 0) || max_iter < 1) return MM_ERR_ARG;
-    return p->precision == MM_FP64
+    return mm_double_fields(p)
                ? adjoint_t<double>(p, m, Hext, dJdm, dJdK, tol, max_iter, iters, resid, (cudaStream_t)stream)
                : adjoint_t<float>(p, m, Hext, dJdm, dJdK, tol, max_iter, iters, resid, (cudaStream_t)stream);
 }
@@ -417,7 +417,7 @@ extern "C" MM_API int mm_set_anisotropy(mm_problem *p, const double *K_cell, voi
     }
     double *tmp = nullptr;
     const bool kdev = mm_is_device_ptr(K_cell);
-    if (p->precision == MM_FP64) {
+    if (mm_double_fields(p)) {
         int rc = mm_copy_user(p->Kc, K_cell, sizeof(double) * N, true, kdev, s);
         if (rc) return rc;
     } else {

@@ -200,7 +200,8 @@ int plan(mm_problem *p)
         }
     }
     if (!p->nrb) {
-        // bulk layout: separate y and z passes
+        // bulk layout: separate y and z passes (double and float only)
+        if (p->precision == MM_F32X2) return MM_ERR_UNSUPPORTED;
         g.bulk = 1;
         g.RB = 1;
         p->rbs[0] = 1;
@@ -352,7 +353,7 @@ extern "C" int mm_setup_geometry(const mm_grid *grid, const mm_material *mat, in
 {
     NvtxRange nvtx_("mm_setup_geometry");
     if (!out || !grid_ok(grid) || !mat) return MM_ERR_ARG;
-    if (precision != MM_FP64 && precision != MM_FP32) return MM_ERR_ARG;
+    if (precision != MM_FP64 && precision != MM_FP32 && precision != MM_F32X2) return MM_ERR_ARG;
     if (!(std::isfinite(mat->Ms) && mat->Ms > 0) || !(std::isfinite(mat->A) && mat->A >= 0) || !std::isfinite(mat->K))
         return MM_ERR_ARG;
     const double un = std::sqrt(mat->u[0] * mat->u[0] + mat->u[1] * mat->u[1] + mat->u[2] * mat->u[2]);
@@ -367,7 +368,7 @@ extern "C" int mm_setup_geometry(const mm_grid *grid, const mm_material *mat, in
     p->mat.K_cell = nullptr;
     p->mat.u_cell = nullptr;
     p->precision = precision;
-    p->esz = precision == MM_FP64 ? 8 : 4;
+    p->esz = precision == MM_FP32 ? 4 : 8;   // MM_F32X2: double fields, tensor as float pairs (8 bytes)
     int rc = plan(p);
     if (rc != MM_OK) { delete p; return rc; }
     cudaGetDevice(&p->dev);

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "../../include/mm.h"
+#include "dfloat.cuh"
 
 #define MM_MU0 (4e-7 * 3.14159265358979323846)
 
@@ -16,6 +17,7 @@
 template <typename T> struct cvec;
 template <> struct cvec<double> { typedef double2 type; };
 template <> struct cvec<float> { typedef float2 type; };
+template <> struct cvec<dfloat> { typedef dcomplex type; };
 
 template <typename V> __device__ __forceinline__ V cmake(decltype(V().x) a, decltype(V().x) b) { V r; r.x = a; r.y = b; return r; }
 template <typename V> __device__ __forceinline__ V cadd(V a, V b) { V r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
@@ -190,16 +192,20 @@ template <typename T> __host__ __device__ __forceinline__ T pick(double d, float
 // Field evaluation modes of the x-inverse/local kernel
 enum { MODE_HEFF = 0, MODE_ENERGY = 1, MODE_MIN = 2 };
 
-template <typename T>
+// T: element type of the fields m, H, g and of the local terms (double or
+// float); F: arithmetic type of the FFTs and the convolution, whose complex
+// values fill the spectrum buffers and the tensor (T itself, or dfloat for
+// MM_F32X2)
+template <typename T, typename F = T>
 struct FieldPtrs {
-    typedef typename cvec<T>::type V;
+    typedef typename cvec<F>::type V;
     const T *m_src;        // field input for MODE_HEFF/ENERGY, or NULL (then mbuf by state)
     T *H_out;              // MODE_HEFF output
     T *mbuf[2];            // minimiser iterate buffers
     T *gbuf[2];            // projected-gradient buffers
     V *W;                  // spectrum [C][nz][ny][3] (x-frequency slowest, component fastest)
     V *W2;                 // bulk layout only: y-transformed spectrum [C][nz][Py][3]
-    const T *Nhat;         // tensor: film [C][max(1,Pz/2)][6][Py/2+1] (x-y transform at real z offsets, scaled by
+    const F *Nhat;         // tensor: film [C][max(1,Pz/2)][6][Py/2+1] (x-y transform at real z offsets, scaled by
                            // -Ms/(Px Py)); bulk [C][Pz/2+1][Py/2+1][6] (octant of the 3-D spectrum,
                            // scaled by -Ms/(Px Py Pz))
     const V *tw_px;        // exp(-2 pi i t/Px), t < Px
@@ -261,6 +267,20 @@ struct mm_problem {
 // per-cell anisotropy pointer); rebuilt on the next mm_adjoint_dK
 void mm_adjoint_invalidate(mm_problem *p);
 
+// field-kernel entry points of each precision (field_fp64.cu, field_fp32.cu, field_f32x2.cu)
+#define MM_DECLARE_FIELD_ENTRIES(SFX)                                                                          \
+    cudaError_t mm_fields_configure_##SFX(const Geom &g, size_t sxf, size_t sx, size_t syz);                  \
+    cudaError_t mm_fields_autotune_##SFX(mm_problem *p, const int *tys, int nty, const int *rbs, int nrb,      \
+                                         cudaStream_t s);                                                      \
+    cudaError_t mm_fields_chain_##SFX(mm_problem *p, const void *m, void *H, const double *hext, int mode,    \
+                                      cudaStream_t s, double hscale);                                         \
+    cudaError_t mm_fields_min_body_##SFX(mm_problem *p, cudaGraphConditionalHandle h, cudaStream_t s,         \
+                                         int use_cond);                                                        \
+    cudaError_t mm_fields_stage_times_##SFX(mm_problem *p, int reps, double *ms, cudaStream_t s);
+MM_DECLARE_FIELD_ENTRIES(fp64)
+MM_DECLARE_FIELD_ENTRIES(fp32)
+MM_DECLARE_FIELD_ENTRIES(f32x2)
+
 // launchers implemented in heff.cu
 int mm_launch_min_body(mm_problem *p, cudaGraphConditionalHandle h, cudaStream_t s, int use_cond);
 int mm_kernel_stage_times(mm_problem *p, int reps, double *ms, const char **names, int *count, cudaStream_t s);
@@ -291,6 +311,8 @@ int mm_tensor_spectrum(mm_problem *p, const double *N_dev, cudaStream_t s);
 
 // helpers (api.cu)
 bool mm_is_device_ptr(const void *ptr);
+// fields of this problem are double (MM_FP64, MM_F32X2) rather than float
+inline bool mm_double_fields(const mm_problem *p) { return p->precision != MM_FP32; }
 // options of a minimisation within range (finite tolerances, known rules)
 bool mm_opts_ok(const mm_min_opts *o);
 // streaming multiprocessors of the current device (queried once per device)

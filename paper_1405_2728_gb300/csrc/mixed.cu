@@ -33,7 +33,7 @@ int transfer(mm_problem *from, mm_problem *to, cudaStream_t s)
 {
     const long n3 = 3 * from->g.N;
     const int blocks = mm_grid_for(n3, 256, 8);
-    if (from->precision == MM_FP64)
+    if (mm_double_fields(from))
         k_transfer<double, float><<<blocks, 256, 0, s>>>(from->st, (const double *)from->mbuf[0],
                                                          (const double *)from->mbuf[1], (float *)to->mbuf[0], n3);
     else
@@ -95,7 +95,7 @@ extern "C" MM_API int mm_hysteresis_sweep_mixed(mm_problem *lo, mm_problem *hi, 
     if (!lo || !hi || !m || !H_list || !mavg || n < 1 || start < 0 || start >= n || !opts_valid(opts_lo) ||
         !opts_valid(opts_hi))
         return MM_ERR_ARG;
-    if (lo->precision != MM_FP32 || hi->precision != MM_FP64 || lo->g.nx != hi->g.nx || lo->g.ny != hi->g.ny ||
+    if (lo->precision != MM_FP32 || !mm_double_fields(hi) || lo->g.nx != hi->g.nx || lo->g.ny != hi->g.ny ||
         lo->g.nz != hi->g.nz)
         return MM_ERR_ARG;
     for (int j = start; j < n; ++j)

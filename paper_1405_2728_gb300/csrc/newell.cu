@@ -249,6 +249,8 @@ int mm_tensor_spectrum(mm_problem *p, const double *N_dev, cudaStream_t s)
             const double fscale = -g.Ms / ((double)g.Px * g.Py);
             if (p->precision == MM_FP64)
                 k_extract_film<double><<<(int)fblocks, 256, 0, s>>>(c, g.Px, g.Py, g.nz, nzf, F, fscale, (double *)p->Nhat);
+            else if (p->precision == MM_F32X2)
+                k_extract_film<dfloat><<<(int)fblocks, 256, 0, s>>>(c, g.Px, g.Py, g.nz, nzf, F, fscale, (dfloat *)p->Nhat);
             else
                 k_extract_film<float><<<(int)fblocks, 256, 0, s>>>(c, g.Px, g.Py, g.nz, nzf, F, fscale, (float *)p->Nhat);
         } else if (p->precision == MM_FP64) {

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "libmmgb.so")
 
 MM_OK, MM_ERR_ARG, MM_ERR_OOM, MM_ERR_CUDA = 0, -1, -2, -3
 MM_ERR_NOT_CONVERGED, MM_ERR_NONFINITE, MM_ERR_TIMEOUT, MM_ERR_UNSUPPORTED = -4, -5, -6, -7
-MM_FP64, MM_FP32 = 0, 1
+MM_FP64, MM_FP32, MM_F32X2 = 0, 1, 2
 MM_STEP_CAYLEY, MM_STEP_NORMALIZE = 0, 1
 MM_TAU_ALTERNATE, MM_TAU_ADAPTIVE = 0, 1
 
@@ -196,7 +196,7 @@ class Problem:
         self.handle = handle
         self.grid = grid
         self.precision = precision
-        self.dtype = np.float64 if precision == MM_FP64 else np.float32
+        self.dtype = np.float32 if precision == MM_FP32 else np.float64
         self.shape = (3, grid.nz, grid.ny, grid.nx)
 
     def close(self):

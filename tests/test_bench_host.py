@@ -47,7 +47,7 @@ def test_kernel_hash_ignores_comments_but_not_code(tmp_path, monkeypatch):
     out = _copy_sources(tmp_path)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.kernel_source_hash() == ref
-    f = out / "heff.cu"
+    f = out / "field_kernels.cuh"
     text = f.read_text()
     f.write_text("/* a new block\n   comment */\n" + text.replace("\n", "  // trailing note\n", 3) + "\n\n")
     assert bench.kernel_source_hash() == ref

@@ -77,3 +77,50 @@ def test_batch_fp32_mixed_with_fp64(mmlib):
         assert np.array_equal(mavg[i], mavg1), i
         assert torch.equal(ms[i], m1), i
     batch.close()
+
+
+def test_batch_with_a_bulk_problem_equals_single_sweeps(mmlib):
+    """A three-dimensional grid (bulk layout) takes the batch's stream path;
+    every member still equals its own single sweep bit for bit."""
+    films = small_films()[:2]
+    cube = inputs.Workload("cube_6", 6, 6, 6, 5e-9, 5e-9, 5e-9, K=2e4)
+    members = films + [cube]
+    probs = [mmlib.mm_setup_geometry(mmlib.make_grid(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz),
+                                     mmlib.make_material(w.Ms, w.A, w.K)) for w in members]
+    assert mmlib.mm_problem_info(probs[-1])["bulk_layout"] == 1
+    F = films[0].fields()[:4]
+    opts = mmlib.make_opts(tol=1e-6)
+    batch = mmlib.mm_batch_create(probs)
+    ms = [dev(w.initial_m()) for w in members]
+    st, mavg, res = mmlib.mm_batch_sweep(batch, ms, F, opts=opts)
+    assert st == mmlib.MM_OK
+    for i, (w, p) in enumerate(zip(members, probs)):
+        m1 = dev(w.initial_m())
+        st1, mavg1, res1 = mmlib.mm_hysteresis_sweep(p, m1, F, opts=opts)
+        assert st1 == mmlib.MM_OK
+        assert np.array_equal(mavg[i], mavg1), i
+        assert torch.equal(ms[i], m1), i
+        assert [r.heff_evals for r in res[i]] == [r.heff_evals for r in res1]
+    batch.close()
+
+
+def test_grouped_batch_repeats_and_resumes(mmlib):
+    """Two sweep calls on one batch (the second resuming at a later field
+    value, with more field values than the first) give what one sweep gives."""
+    films = small_films()[:3]
+    probs = [mmlib.mm_setup_geometry(mmlib.make_grid(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz),
+                                     mmlib.make_material(w.Ms, w.A, w.K)) for w in films]
+    F = films[0].fields()
+    opts = mmlib.make_opts(tol=1e-6)
+    b1 = mmlib.mm_batch_create(probs)
+    ms1 = [dev(w.initial_m()) for w in films]
+    _, mavg1, _ = mmlib.mm_batch_sweep(b1, ms1, F, opts=opts)
+    b1.close()
+    b2 = mmlib.mm_batch_create(probs)
+    ms2 = [dev(w.initial_m()) for w in films]
+    mmlib.mm_batch_sweep(b2, ms2, F[:4], opts=opts)
+    _, mavg2, _ = mmlib.mm_batch_sweep(b2, ms2, F, start=4, opts=opts)
+    for i in range(len(films)):
+        assert np.array_equal(mavg1[i][4:], mavg2[i][4:]), i
+        assert torch.equal(ms1[i], ms2[i]), i
+    b2.close()
