@@ -185,7 +185,7 @@ int plan(mm_problem *p)
     g.lpz = ilog2i(g.Pz);
     g.Gz = g.Pz >= 8 ? g.Pz / 8 : 1;
     // admissible launch shapes; mm_autotune picks among them after setup
-    const size_t smax = 200 * 1024;
+    const size_t smax = MM_SMEM_CAP;
     g.bulk = 0;
     p->nrb = 0;
     if (g.Pz <= 8) {

@@ -380,9 +380,10 @@ template <typename T> cudaError_t build_group(mm_batch *b, Group<T> &G)
     if ((e = cudaMalloc((void **)&G.act.base, sizeof(int) * (1 + nf + 3 * ((size_t)nf + 1))))) return e;
     if ((e = cudaMemset(G.act.base, 0, sizeof(int) * (1 + nf + 3 * ((size_t)nf + 1))))) return e;
     if (nf == 0) return cudaSuccess;
-    if ((e = cudaFuncSetAttribute(k_xfwd_group<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.sm_xf)) ||
-        (e = cudaFuncSetAttribute(k_yz_group<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.sm_yz)) ||
-        (e = cudaFuncSetAttribute(k_xinv_group<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.sm_x)))
+    if (G.sm_xf > MM_SMEM_CAP || G.sm_yz > MM_SMEM_CAP || G.sm_x > MM_SMEM_CAP) return cudaErrorInvalidValue;
+    if ((e = cudaFuncSetAttribute(k_xfwd_group<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, MM_SMEM_CAP)) ||
+        (e = cudaFuncSetAttribute(k_yz_group<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, MM_SMEM_CAP)) ||
+        (e = cudaFuncSetAttribute(k_xinv_group<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, MM_SMEM_CAP)))
         return e;
     // persistent grids: as many CTAs as are resident on all SMs at once
     int r0 = 0, r1 = 0, r2 = 0;

@@ -214,9 +214,11 @@ template <typename T> cudaError_t bulk_conv_t(const Geom &g, const FieldPtrs<T> 
     return cudaGetLastError();
 }
 
+// the bytes a launch needs must fit the common cap, which every kernel is given
 template <typename F> cudaError_t smem_attr(F *f, size_t bytes)
 {
-    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (bytes > (size_t)MM_SMEM_CAP) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, MM_SMEM_CAP);
 }
 
 template <typename T> cudaError_t configure_t(const Geom &g)

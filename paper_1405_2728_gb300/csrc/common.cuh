@@ -281,6 +281,15 @@ MM_DECLARE_FIELD_ENTRIES(fp64)
 MM_DECLARE_FIELD_ENTRIES(fp32)
 MM_DECLARE_FIELD_ENTRIES(f32x2)
 
+// Largest dynamic shared memory any field-kernel launch may use (the
+// planner keeps every launch shape within it).  Kernels get this limit as
+// their MaxDynamicSharedMemorySize attribute once and for all: the attribute
+// belongs to the kernel function, shared by every problem of the process, so
+// setting it to one problem's own need would refuse the larger launches of
+// problems configured before it.  It only permits launches; nothing is
+// reserved by it.
+#define MM_SMEM_CAP (200 * 1024)
+
 // launchers implemented in heff.cu
 int mm_launch_min_body(mm_problem *p, cudaGraphConditionalHandle h, cudaStream_t s, int use_cond);
 int mm_kernel_stage_times(mm_problem *p, int reps, double *ms, const char **names, int *count, cudaStream_t s);

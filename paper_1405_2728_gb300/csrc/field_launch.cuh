@@ -79,9 +79,11 @@ cudaError_t launch_conv(const Geom &g, const FieldPtrs<T, F> &P, cudaStream_t s)
     return launch_yz_any<T, F>(g, P, s);
 }
 
+// the bytes a launch needs must fit the common cap, which every kernel is given
 template <typename K> cudaError_t smem_attr(K *f, size_t bytes)
 {
-    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (bytes > (size_t)MM_SMEM_CAP) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, MM_SMEM_CAP);
 }
 
 // dynamic shared memory limits of the instances this geometry launches

@@ -136,6 +136,12 @@ def film_512x256x4() -> Workload:
     return Workload("film_512x256x4", 512, 256, 4, 2000e-9 / 512, 1000e-9 / 256, 5e-9)
 
 
+def film_128x64x2() -> Workload:
+    """500 x 250 x 10 nm film on 128 x 64 x 2 cells (3.90625 x 3.90625 x 5 nm) with the
+    uniform material of the 512 x 256 x 4 film: a quarter-size loop at the same cell size."""
+    return Workload("film_128x64x2", 128, 64, 2, 500e-9 / 128, 250e-9 / 64, 5e-9)
+
+
 def film_128x64x2_random_K() -> Workload:
     """500 x 250 x 10 nm film on 128 x 64 x 2 cells, per-cell K uniform in [300, 700] J/m^3."""
     w = Workload("film_128x64x2_randK", 128, 64, 2, 500e-9 / 128, 250e-9 / 64, 5e-9)
@@ -206,6 +212,7 @@ WORKLOADS = {
     "film_32x16x1": film_32x16x1,
     "film_512x256x4": film_512x256x4,
     "film_128x64x2_randK": film_128x64x2_random_K,
+    "film_128x64x2": film_128x64x2,
 }
 
 # bulk workloads (a different material and field protocol)

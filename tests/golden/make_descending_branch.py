@@ -1,21 +1,24 @@
-"""Write the oracle's descending branch of the 512 x 256 x 4 film loop.
+"""Write the oracle's descending branch of a film's hysteresis loop.
 
 Calls only the CPU oracle (``oracle/``) and the seeded input generators.  The
-workload is the thin film of Section 4 (2000 x 1000 x 20 nm on 512 x 256 x 4
-cells, Ms = 8e5 A/m, A = 1.3e-11 J/m, K = 500 J/m^3 along x, field 1 degree
-off x in 1 mT steps, stop at max|m x H|/Ms < 1e-5).  The sweep starts at
+default workload is the thin film of Section 4 (2000 x 1000 x 20 nm on
+512 x 256 x 4 cells, Ms = 8e5 A/m, A = 1.3e-11 J/m, K = 500 J/m^3 along x,
+field 1 degree off x in 1 mT steps, stop at max|m x H|/Ms < 1e-5);
+``--workload film_128x64x2`` takes the same material on a 500 x 250 x 10 nm
+film with the same cells, whose whole branch the oracle finishes in about an
+hour on a few host cores.  The sweep starts at
 +50 mT from the seeded tilted state and runs down the descending branch one
 field value at a time, warm-started from the previous magnetisation, until
 the first value past 0 mT whose mean magnetisation points against the field
 (the switching field).  That covers the remanence (0 mT) and the switching
 field, the two loop results compared against the CUDA library.
 
-Output (``film_512x256x4_descending.json``): the input hash, and per field
+Output (``<workload>_descending.json``): the input hash, and per field
 value the field (A/m), <m>, the evaluation count, the final torque and the
 convergence flag.  A state file given by ``--state`` lets a long run resume;
 it holds the current magnetisation and is not part of the stored values.
 
-Usage:  python tests/golden/make_film_512x256x4_descending.py [--state PATH] [--workers N]
+Usage:  python tests/golden/make_film_512x256x4_descending.py [--workload NAME] [--state PATH] [--workers N]
 """
 from __future__ import annotations
 
@@ -34,7 +37,7 @@ sys.path.insert(0, ROOT)
 from oracle import micromag as om  # noqa: E402
 from paper_1405_2728_gb300 import inputs  # noqa: E402
 
-OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "film_512x256x4_descending.json")
+HERE = os.path.dirname(os.path.abspath(__file__))
 
 
 def input_hash(w, m0, H_list) -> str:
@@ -51,9 +54,11 @@ def main():
     ap.add_argument("--state", default=None, help="resume file (npz) for the current magnetisation")
     ap.add_argument("--workers", type=int, default=None, help="FFT threads of the oracle")
     ap.add_argument("--max-iter", type=int, default=100000)
+    ap.add_argument("--workload", default="film_512x256x4", choices=["film_512x256x4", "film_128x64x2"])
     args = ap.parse_args()
 
-    w = inputs.film_512x256x4()
+    w = inputs.WORKLOADS[args.workload]()
+    OUT = os.path.join(HERE, f"{w.name}_descending.json")
     prob = om.Problem(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, Ms=w.Ms, A=w.A, K=w.K, u=w.u)
     H_all = w.fields()
     n_desc = 101  # +50 ... -50 mT
