@@ -205,7 +205,7 @@ def survey_flops(info):
     return out
 
 
-KERNEL_SOURCES = ("common.cuh", "fft.cuh", "field_kernels.cuh", "heff.cu")  # what the film field kernels compile from
+KERNEL_SOURCES = ("fft.cuh", "dfloat.cuh", "field_kernels.cuh")  # the device code of the film field kernels
 
 
 def kernel_source_hash():

@@ -237,7 +237,11 @@ int plan(mm_problem *p)
     for (int ty = 1; ty <= 16 && ty <= next_pow2(gr.ny); ty *= 2)
         if (3 * ty * g.Gx <= 768 && mm_smem_x_for(p, ty) <= smax) p->tys[p->nty++] = ty;
     if (!p->nty) return MM_ERR_UNSUPPORTED;
-    g.TY = g.TYF = p->tys[p->nty - 1];
+    // untuned problems (below the autotuner's size) take the smallest tile:
+    // the most CTAs per stage, which is what their latency-bound kernels need
+    // (the 32 x 16 x 1 film: 49 us per evaluation against 69 us with the
+    // widest tile); the autotuner replaces it on larger problems
+    g.TY = g.TYF = p->tys[0];
     g.lty = g.ltyf = ilog2i(g.TY);
     // partial sums are sized for the smallest tile (most CTAs)
     p->nblk_x = ((gr.ny + p->tys[0] - 1) / p->tys[0]) * gr.nz;
@@ -430,7 +434,7 @@ extern "C" int mm_setup_geometry(const mm_grid *grid, const mm_material *mat, in
         // times are mostly noise, so a timed choice would change from run to run.
         // The shape changes the order of the partial sums, and through it the
         // rounding that decides a minimiser's branch at a switching field.
-        // They keep the planner's defaults (largest tile, largest row batch).
+        // They keep the planner's defaults (smallest tile, largest row batch).
         if (p->g.N >= 65536) {
             NvtxRange nvtx_tune("mm_autotune");
             if ((rc = mm_autotune(p, p->tys, p->nty, p->rbs, p->nrb, s)) != MM_OK) break;
@@ -540,7 +544,7 @@ extern "C" int mm_minimize(mm_problem *p, void *m, const double Hext[3], const m
     int rc;
     if ((rc = copy_user(p->mbuf[0], m, F, true, mdev, s))) return rc;
     if ((rc = mm_launch_init_state(p, Hext, opts, 1, s))) return rc;
-    CK(cudaGraphLaunch(p->gexec, s), "cudaGraphLaunch");
+    if ((rc = mm_launch_loop(p, s))) return rc;
     if ((rc = mm_launch_copy_result(p, mdev ? m : p->stage_out, s))) return rc;
     if (!mdev && (rc = copy_user(m, p->stage_out, F, false, true, s))) return rc;
     CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(MinState), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync");
@@ -570,7 +574,7 @@ extern "C" int mm_hysteresis_sweep(mm_problem *p, void *m, const double *H_list,
     if ((rc = copy_user(p->mbuf[0], m, F, true, mdev, s))) return rc;
     for (int i = start; i < n; ++i) {
         if ((rc = mm_launch_init_state(p, H_list + 3 * i, opts, i == start, s))) return rc;
-        CK(cudaGraphLaunch(p->gexec, s), "cudaGraphLaunch");
+        if ((rc = mm_launch_loop(p, s))) return rc;
         if ((rc = mm_launch_record(p, i, s))) return rc;
     }
     if ((rc = mm_launch_copy_result(p, mdev ? m : p->stage_out, s))) return rc;

@@ -56,6 +56,12 @@ struct GActive {
 
 struct GItem { int film, bx, by; };
 
+// A problem group as the init and advance kernels see it.  The descriptor
+// layout does not depend on the field type (Geom, then pointers), so both
+// precisions are read through the double view for the state and item counts.
+struct GActive;
+
+
 // per problem and sweep call: what the init kernel writes into its state
 struct GInit {
     MinState *st;
@@ -84,6 +90,13 @@ __device__ __forceinline__ void load_film(GFilm<T> &f, const GFilm<T> *src)
 
 // the work item behind virtual index v of stage s (binary search over the
 // active problems' prefix sums)
+struct GRef {
+    const GFilm<double> *films;
+    int nf;
+    GActive act;
+};
+static_assert(sizeof(GFilm<double>) == sizeof(GFilm<float>), "descriptor layout is precision independent");
+
 __device__ __forceinline__ GItem active_item(const GActive &A, const int *first, const GItem *items, int s, int v)
 // first[s * nf + f]: where problem f's items start in stage s's item array
 {
@@ -153,8 +166,7 @@ __global__ void __launch_bounds__(768) k_xinv_group(const GFilm<T> *films, const
 
 // compacted work lists of the problems still running (one CTA); `first`
 // lists, per problem, where its items start in each stage's item array
-template <typename T>
-__device__ void build_active(const GFilm<T> *films, int nf, GActive A)
+__device__ void build_active(const GFilm<double> *films, int nf, GActive A)
 {
     if (threadIdx.x != 0 || nf == 0) return;
     int na = 0;
@@ -193,14 +205,12 @@ __device__ void init_one(GInit *init, int i, int j, const double *H, const GCtl 
 }
 
 // before the loop: every problem at the sweep's first field value
-__global__ void k_group_init(GInit *init, int n, const double *H, const GCtl *ctl, const GFilm<double> *f64,
-                             int n64, GActive a64, const GFilm<float> *f32, int n32, GActive a32)
+__global__ void k_group_init(GInit *init, int n, const double *H, const GCtl *ctl, const GRef *refs, int nrefs)
 {
     const GCtl c = *ctl;
     for (int i = threadIdx.x; i < n; i += blockDim.x) init_one(init, i, c.start, H, c);
     __syncthreads();
-    build_active(f64, n64, a64);
-    build_active(f32, n32, a32);
+    for (int r = 0; r < nrefs; ++r) build_active(refs[r].films, refs[r].nf, refs[r].act);
 }
 
 // After every iteration: each problem whose minimisation at its field value
@@ -208,8 +218,7 @@ __global__ void k_group_init(GInit *init, int n, const double *H, const GCtl *ct
 // non-finite value) records that field value and starts its next one, so
 // problems advance through the sweep at their own pace; then the work lists
 // of the next iteration, and the loop goes on while any problem runs.
-__global__ void k_group_advance(GInit *init, int n, const double *H, const GCtl *ctl, const GFilm<double> *f64,
-                                int n64, GActive a64, const GFilm<float> *f32, int n32, GActive a32,
+__global__ void k_group_advance(GInit *init, int n, const double *H, const GCtl *ctl, const GRef *refs, int nrefs,
                                 cudaGraphConditionalHandle h)
 {
     const GCtl c = *ctl;
@@ -226,11 +235,13 @@ __global__ void k_group_advance(GInit *init, int n, const double *H, const GCtl 
         else init[i].j = c.n;
     }
     __syncthreads();
-    build_active(f64, n64, a64);
-    build_active(f32, n32, a32);
     if (threadIdx.x != 0) return;
-    const unsigned go = ((n64 ? a64.nact() : 0) + (n32 ? a32.nact() : 0)) > 0 ? 1u : 0u;
-    cudaGraphSetConditional(h, go);
+    int active = 0;
+    for (int r = 0; r < nrefs; ++r) {
+        build_active(refs[r].films, refs[r].nf, refs[r].act);
+        if (refs[r].nf) active += refs[r].act.nact();
+    }
+    cudaGraphSetConditional(h, active > 0 ? 1u : 0u);
 }
 
 // device tables of one precision group
@@ -258,8 +269,13 @@ struct mm_batch {
     cudaEvent_t start_ev = nullptr;
     // grouped path
     bool grouped = false;
-    Group<double> g64;
-    Group<float> g32;
+    // groups by precision and size class: large problems (>= 65536 cells)
+    // and small ones; each group's stages run as a branch of its own in the
+    // loop body, so the groups' kernels overlap on the GPU
+    std::vector<Group<double>> g64;
+    std::vector<Group<float>> g32;
+    GRef *refs_dev = nullptr;
+    int nrefs = 0;
     GInit *init_dev = nullptr;   // [nprob]
     GCtl *ctl_dev = nullptr;
     double *H_dev = nullptr;     // [cap][3]
@@ -311,8 +327,9 @@ void free_batch(mm_batch *b)
     if (b->start_ev) cudaEventDestroy(b->start_ev);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    free_group(b->g64);
-    free_group(b->g32);
+    for (auto &G : b->g64) free_group(G);
+    for (auto &G : b->g32) free_group(G);
+    if (b->refs_dev) cudaFree(b->refs_dev);
     if (b->init_dev) cudaFree(b->init_dev);
     if (b->ctl_dev) cudaFree(b->ctl_dev);
     if (b->H_dev) cudaFree(b->H_dev);
@@ -421,16 +438,20 @@ template <typename T> void launch_group(const Group<T> &G, cudaStream_t s)
 int build_batch_graph(mm_batch *b)
 {
     const int n = (int)b->probs.size();
-    const int n64 = (int)b->g64.members.size(), n32 = (int)b->g32.members.size();
+    const int ng = (int)(b->g64.size() + b->g32.size());
     cudaStream_t cs;
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e) { mm_set_cuda_error(e, "cudaStreamCreate"); return MM_ERR_CUDA; }
+    std::vector<cudaStream_t> br(ng, nullptr);
+    std::vector<cudaEvent_t> ev(ng + 1, nullptr);
     do {
+        for (int i = 0; i < ng && !e; ++i) e = cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking);
+        for (int i = 0; i <= ng && !e; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+        if (e) break;
         if ((e = cudaGraphCreate(&b->graph, 0))) break;
         if ((e = cudaGraphConditionalHandleCreate(&b->cond, b->graph, 1, cudaGraphCondAssignDefault))) break;
         if ((e = cudaStreamBeginCaptureToGraph(cs, b->graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed))) break;
-        k_group_init<<<1, 256, 0, cs>>>(b->init_dev, n, b->H_dev, b->ctl_dev, b->g64.films, n64, b->g64.act,
-                                        b->g32.films, n32, b->g32.act);
+        k_group_init<<<1, 256, 0, cs>>>(b->init_dev, n, b->H_dev, b->ctl_dev, b->refs_dev, b->nrefs);
         cudaGraph_t g0 = b->graph;
         if ((e = cudaStreamEndCapture(cs, &g0))) break;
         cudaGraphNode_t init_node;
@@ -445,10 +466,23 @@ int build_batch_graph(mm_batch *b)
         if ((e = cudaGraphAddNode(&cond_node, b->graph, &init_node, nullptr, 1, &np))) break;
         cudaGraph_t body = np.conditional.phGraph_out[0];
         if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed))) break;
-        launch_group(b->g64, cs);
-        launch_group(b->g32, cs);
-        k_group_advance<<<1, 256, 0, cs>>>(b->init_dev, n, b->H_dev, b->ctl_dev, b->g64.films, n64, b->g64.act,
-                                           b->g32.films, n32, b->g32.act, b->cond);
+        // one branch per group: fork from the capture stream, join before the advance kernel
+        cudaEventRecord(ev[ng], cs);
+        int gi = 0;
+        for (auto &G : b->g64) {
+            cudaStreamWaitEvent(br[gi], ev[ng], 0);
+            launch_group(G, br[gi]);
+            cudaEventRecord(ev[gi], br[gi]);
+            ++gi;
+        }
+        for (auto &G : b->g32) {
+            cudaStreamWaitEvent(br[gi], ev[ng], 0);
+            launch_group(G, br[gi]);
+            cudaEventRecord(ev[gi], br[gi]);
+            ++gi;
+        }
+        for (int i = 0; i < ng; ++i) cudaStreamWaitEvent(cs, ev[i], 0);
+        k_group_advance<<<1, 256, 0, cs>>>(b->init_dev, n, b->H_dev, b->ctl_dev, b->refs_dev, b->nrefs, b->cond);
         cudaGraph_t g1 = body;
         const cudaError_t le = cudaGetLastError();
         e = cudaStreamEndCapture(cs, &g1);
@@ -456,6 +490,8 @@ int build_batch_graph(mm_batch *b)
         if (e) break;
         if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0))) break;
     } while (0);
+    for (auto x : br) if (x) cudaStreamDestroy(x);
+    for (auto x : ev) if (x) cudaEventDestroy(x);
     cudaStreamDestroy(cs);
     if (e) { mm_set_cuda_error(e, "batch graph"); return MM_ERR_CUDA; }
     return MM_OK;
@@ -505,13 +541,31 @@ int harmonise_tiles(mm_batch *b, const std::vector<int> &members)
 
 int create_grouped(mm_batch *b)
 {
-    for (size_t i = 0; i < b->probs.size(); ++i)
-        (b->probs[i]->precision == MM_FP64 ? b->g64.members : b->g32.members).push_back((int)i);
+    // groups by precision and size class (the setup autotuner's threshold):
+    // large problems keep their tuned tiles and carry most of the work; small
+    // ones share wider tiles; each group's stages form a branch of their own
+    std::vector<int> m64[2], m32[2];
+    for (size_t i = 0; i < b->probs.size(); ++i) {
+        const int large = b->probs[i]->g.N >= 65536;
+        (b->probs[i]->precision == MM_FP64 ? m64[large] : m32[large]).push_back((int)i);
+    }
+    for (int c = 1; c >= 0; --c) {
+        if (!m64[c].empty()) { b->g64.emplace_back(); b->g64.back().members = m64[c]; }
+        if (!m32[c].empty()) { b->g32.emplace_back(); b->g32.back().members = m32[c]; }
+    }
     int rc;
-    if ((rc = harmonise_tiles(b, b->g64.members)) || (rc = harmonise_tiles(b, b->g32.members))) return rc;
-    cudaError_t e;
-    if ((e = build_group(b, b->g64)) || (e = build_group(b, b->g32))) { mm_set_cuda_error(e, "batch tables"); return MM_ERR_CUDA; }
-    if ((e = cudaMalloc((void **)&b->init_dev, sizeof(GInit) * b->probs.size())) ||
+    for (auto &G : b->g64) if ((rc = harmonise_tiles(b, G.members))) return rc;
+    for (auto &G : b->g32) if ((rc = harmonise_tiles(b, G.members))) return rc;
+    cudaError_t e = cudaSuccess;
+    for (auto &G : b->g64) if (!e) e = build_group(b, G);
+    for (auto &G : b->g32) if (!e) e = build_group(b, G);
+    if (e) { mm_set_cuda_error(e, "batch tables"); return MM_ERR_CUDA; }
+    std::vector<GRef> refs;
+    for (auto &G : b->g64) refs.push_back({G.films, (int)G.members.size(), G.act});
+    for (auto &G : b->g32) refs.push_back({reinterpret_cast<const GFilm<double> *>(G.films), (int)G.members.size(), G.act});
+    b->nrefs = (int)refs.size();
+    if ((e = upload(&b->refs_dev, refs)) ||
+        (e = cudaMalloc((void **)&b->init_dev, sizeof(GInit) * b->probs.size())) ||
         (e = cudaMalloc((void **)&b->ctl_dev, sizeof(GCtl))) || (e = cudaMalloc((void **)&b->H_dev, sizeof(double) * 3))) {
         mm_set_cuda_error(e, "cudaMalloc(batch)");
         return MM_ERR_OOM;
@@ -582,8 +636,7 @@ int sweep_streams(mm_batch *b, void *const *m_list, const double *H_list, int n,
             mm_problem *p = b->probs[i];
             cudaStream_t si = b->streams[i];
             if ((rc = mm_launch_init_state(p, H_list + 3 * j, opts, j == start, si))) break;
-            e = cudaGraphLaunch(p->gexec, si);
-            if (e) { mm_set_cuda_error(e, "cudaGraphLaunch(batch)"); rc = MM_ERR_CUDA; break; }
+            if ((rc = mm_launch_loop(p, si))) break;
             rc = mm_launch_record(p, j, si);
         }
     for (size_t i = 0; i < P && rc == MM_OK; ++i) {
@@ -642,7 +695,10 @@ int sweep_grouped(mm_batch *b, void *const *m_list, const double *H_list, int n,
     ctl.tau_rule = opts->tau_rule;
     ctl.timeout_ns = opts->timeout_s > 0 ? (unsigned long long)(opts->timeout_s * 1e9) : 0ull;
     ctl.kappa = opts->tau_kappa > 0 ? opts->tau_kappa : 0.5;
-    if ((e = refresh_group(b, b->g64, s)) || (e = refresh_group(b, b->g32, s)) ||
+    e = cudaSuccess;
+    for (auto &G : b->g64) if (!e) e = refresh_group(b, G, s);
+    for (auto &G : b->g32) if (!e) e = refresh_group(b, G, s);
+    if (e ||
         (e = cudaMemcpyAsync(b->init_dev, init.data(), sizeof(GInit) * P, cudaMemcpyHostToDevice, s)) ||
         (e = cudaMemcpyAsync(b->ctl_dev, &ctl, sizeof ctl, cudaMemcpyHostToDevice, s)) ||
         (e = cudaMemcpyAsync(b->H_dev, H_list, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, s))) {

@@ -263,6 +263,9 @@ struct mm_problem {
     int adj_nblk;
 };
 
+// one minimisation on the device: a launch of the problem's minimiser graph (heff.cu)
+int mm_launch_loop(mm_problem *p, cudaStream_t s);
+
 // drop the adjoint's loop graph (it bakes in kernel parameters such as the
 // per-cell anisotropy pointer); rebuilt on the next mm_adjoint_dK
 void mm_adjoint_invalidate(mm_problem *p);

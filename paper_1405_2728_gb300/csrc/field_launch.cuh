@@ -4,6 +4,7 @@
 // library builds in parallel.
 #pragma once
 
+#include <algorithm>
 #include <cstring>
 #include <type_traits>
 

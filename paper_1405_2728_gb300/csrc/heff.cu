@@ -171,6 +171,13 @@ int mm_kernel_stage_times(mm_problem *p, int reps, double *ms, const char **name
     return MM_OK;
 }
 
+int mm_launch_loop(mm_problem *p, cudaStream_t s)
+{
+    const cudaError_t e = cudaGraphLaunch(p->gexec, s);
+    if (e) { mm_set_cuda_error(e, "cudaGraphLaunch"); return MM_ERR_CUDA; }
+    return MM_OK;
+}
+
 int mm_launch_init_state(mm_problem *p, const double Hext[3], const mm_min_opts *o, int reset_base, cudaStream_t s)
 {
     double tau0 = o->tau0 > 0 ? o->tau0 : 1e-2 / p->g.Ms;

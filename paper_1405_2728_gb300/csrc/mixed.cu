@@ -112,12 +112,10 @@ extern "C" MM_API int mm_hysteresis_sweep_mixed(mm_problem *lo, mm_problem *hi, 
     if ((rc = mm_launch_init_state(hi, H_list + 3 * start, opts_hi, 1, s))) return rc;
     for (int j = start; j < n; ++j) {
         if ((rc = transfer(hi, lo, s)) || (rc = mm_launch_init_state(lo, H_list + 3 * j, opts_lo, 1, s))) return rc;
-        cudaError_t e = cudaGraphLaunch(lo->gexec, s);
-        if (e) { mm_set_cuda_error(e, "cudaGraphLaunch(float)"); return MM_ERR_CUDA; }
+        if ((rc = mm_launch_loop(lo, s))) return rc;
         if ((rc = mm_launch_record(lo, j, s))) return rc;
         if ((rc = transfer(lo, hi, s)) || (rc = mm_launch_init_state(hi, H_list + 3 * j, opts_hi, 1, s))) return rc;
-        e = cudaGraphLaunch(hi->gexec, s);
-        if (e) { mm_set_cuda_error(e, "cudaGraphLaunch(double)"); return MM_ERR_CUDA; }
+        if ((rc = mm_launch_loop(hi, s))) return rc;
         if ((rc = mm_launch_record(hi, j, s))) return rc;
     }
     if ((rc = mm_launch_copy_result(hi, mdev ? m : hi->stage_out, s))) return rc;

@@ -18,7 +18,7 @@ value the field (A/m), <m>, the evaluation count, the final torque and the
 convergence flag.  A state file given by ``--state`` lets a long run resume;
 it holds the current magnetisation and is not part of the stored values.
 
-Usage:  python tests/golden/make_film_512x256x4_descending.py [--workload NAME] [--state PATH] [--workers N]
+Usage:  python tests/golden/make_oracle_loop.py [--workload NAME] [--state PATH] [--workers N]
 """
 from __future__ import annotations
 
@@ -55,13 +55,15 @@ def main():
     ap.add_argument("--workers", type=int, default=None, help="FFT threads of the oracle")
     ap.add_argument("--max-iter", type=int, default=100000)
     ap.add_argument("--workload", default="film_512x256x4", choices=["film_512x256x4", "film_128x64x2"])
+    ap.add_argument("--whole-loop", action="store_true",
+                    help="all 201 field values (descending and ascending branch), not just past the switch")
     args = ap.parse_args()
 
     w = inputs.WORKLOADS[args.workload]()
-    OUT = os.path.join(HERE, f"{w.name}_descending.json")
+    OUT = os.path.join(HERE, f"{w.name}_{'loop' if args.whole_loop else 'descending'}.json")
     prob = om.Problem(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, Ms=w.Ms, A=w.A, K=w.K, u=w.u)
     H_all = w.fields()
-    n_desc = 101  # +50 ... -50 mT
+    n_desc = len(H_all) if args.whole_loop else 101  # +50 ... -50 mT (and back)
     H_desc = H_all[:n_desc]
     m0 = w.initial_m()
     key = input_hash(w, m0, H_all)
@@ -95,7 +97,9 @@ def main():
         rec["max_torque"].append(float(r.max_torque))
         rec["converged"].append(bool(r.converged))
         rec["seconds"].append(round(time.time() - t0, 3))
-        if b_mT < 0 and float(mavg @ hhat) < 0:
+        if args.whole_loop:
+            rec["complete"] = n + 1 == n_desc
+        elif b_mT < 0 and float(mavg @ hhat) < 0:
             rec["complete"] = True
         tmp = OUT + ".tmp"
         with open(tmp, "w") as f:
