@@ -1,5 +1,5 @@
-// Double-float ("double-word") arithmetic for the FFT and convolution stages
-// of the MM_F32X2 precision: a value is the unevaluated sum hi + lo of two
+// Double-float ("double-word") arithmetic of the MM_F32X2 precision (its
+// fields, FFTs, convolution and local terms): a value is the unevaluated sum hi + lo of two
 // floats with |lo| <= ulp(hi)/2, about 48 significant bits, computed on the
 // FP32 pipes (64 times the FP64 FMA rate on this GPU).
 //
@@ -61,4 +61,31 @@ __device__ __forceinline__ dfloat &operator*=(dfloat &a, dfloat b) { a = a * b; 
 
 // the double nearest to hi + lo (one rounding: the sum of two floats is exact in double)
 __device__ __forceinline__ double df_to_double(dfloat a) { return (double)a.hi + (double)a.lo; }
+
+// Quotient by long division: q1 = a.hi / b.hi (correctly rounded), the
+// remainder a - b q1 formed in double-word arithmetic, and one correction
+// q2 = r.hi / b.hi.  The error of q1 + q2 is that of q2 (a relative 2^-24 of a
+// term 2^-24 times smaller than q1) plus the double-word rounding of the
+// remainder: a few units of 2^-48 relative.
+__device__ __forceinline__ dfloat operator/(dfloat a, dfloat b)
+{
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const dfloat r = a - b * dfloat(q1, 0.0f);
+    const float q2 = __fdiv_rn(r.hi, b.hi);
+    return df_fast2sum(q1, q2);
+}
+
+// 1 / sqrt(a) for a > 0: the correctly rounded float y0 = 1/sqrt(a.hi), then
+// one Newton step for f(y) = 1/y^2 - a, y1 = y0 + y0 (1 - a y0^2) / 2, with
+// the residual 1 - a y0^2 in double-word arithmetic (y0^2 exact by one FMA).
+// y0 has relative error <= 2^-24 (plus 2^-25 from dropping a.lo), the step
+// squares it: about 2^-47 relative.
+__device__ __forceinline__ dfloat df_rsqrt(dfloat a)
+{
+    const float y0 = __frsqrt_rn(a.hi);
+    const float p = __fmul_rn(y0, y0);
+    const dfloat y2(p, fmaf(y0, y0, -p));
+    const dfloat e = dfloat(1.0f, 0.0f) - a * y2;
+    return df_fast2sum(y0, __fmul_rn(__fmul_rn(0.5f, y0), e.hi));
+}
 #endif
