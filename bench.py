@@ -40,7 +40,7 @@ FP64_FMA_PER_SM_CLK = 2
 FP32_FMA_PER_SM_CLK = 128
 DW_ADD_INSTRUCTIONS = 11      # FP32 instructions of one double-word (float pair) addition
 PRECISIONS = {"fp64": 0, "fp32": 1, "f32x2": 2}   # mm.MM_FP64, mm.MM_FP32, mm.MM_F32X2
-DTYPE_LABEL = {"fp64": "f64", "fp32": "f32", "f32x2": "f64 fields, f32x2 (double-word) FFT and convolution"}
+DTYPE_LABEL = {"fp64": "f64", "fp32": "f32", "f32x2": "f32x2 (double-word) fields, FFT, convolution and local terms"}
 
 
 def dist_env():
@@ -366,6 +366,8 @@ def run_mixed_loop(args, w, dev):
     lo = mm.mm_setup_geometry(grid, mat, mm.MM_FP32)
     hi = mm.mm_setup_geometry(grid, mat, PRECISIONS[args.mixed_hi])
     F = w.fields()
+    if args.mixed_tol is None:
+        args.mixed_tol = 1e-4 if args.mixed_hi == "f32x2" else 3e-5
     o_lo = mm.make_opts(tol=args.mixed_tol, max_iter=20000)
     o_hi = mm.make_opts(tol=w.tol, max_iter=args.max_iter)
     stream = torch.cuda.current_stream(dev)
@@ -590,7 +592,9 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "f32x2", "mixed"],
                     help="mixed: FP32 minimisation to --mixed-tol, then FP64 to the final tolerance (with --full-loop)")
-    ap.add_argument("--mixed-tol", type=float, default=3e-5)
+    ap.add_argument("--mixed-tol", type=float, default=None,
+                    help="hand-over tolerance of --precision mixed (default: 3e-5 before FP64, 1e-4 before f32x2, "
+                         "the fastest of those measured for each)")
     ap.add_argument("--mixed-hi", default="fp64", choices=["fp64", "f32x2"],
                     help="precision of the second (final-tolerance) phase of --precision mixed")
     ap.add_argument("--workload", default="film_512x256x4")

@@ -70,10 +70,12 @@ typedef enum {
 } mm_status;
 
 /* Element type and arithmetic of the field path.  MM_F32X2 (an extension):
- * fields in double as for MM_FP64, the FFTs and the demagnetisation
- * convolution in double-float arithmetic (pairs of floats, about 48
- * significant bits, run on the FP32 pipes), the local terms, the step and
- * the reductions in double; film-layout grids only (see mm_setup_geometry). */
+ * the caller's arrays are double as for MM_FP64; inside, the iterates, the
+ * FFTs, the demagnetisation convolution, the local terms, the step and the
+ * per-CTA sums use double-float arithmetic (pairs of floats, about 48
+ * significant bits, run on the FP32 pipes), and the sums across CTAs,
+ * the step size and the stop rule are double; film-layout grids only (see
+ * mm_setup_geometry). */
 enum { MM_FP64 = 0, MM_FP32 = 1, MM_F32X2 = 2 };
 enum { MM_STEP_CAYLEY = 0, MM_STEP_NORMALIZE = 1 };  /* update rule, see mm_min_opts */
 enum { MM_TAU_ALTERNATE = 0, MM_TAU_ADAPTIVE = 1 };  /* step-size rule, see mm_min_opts */
@@ -141,12 +143,14 @@ MM_API int mm_newell_static(const mm_grid *grid, double *N_dev, void *stream);
  * power of two >= 2n-1, and >= 2 along x), times the admissible launch
  * shapes of the field kernels on this problem and keeps the fastest, and
  * captures the minimiser's CUDA graph.  precision = MM_FP64 or MM_FP32: element type of m/H and of the FFT
- * and stencil arithmetic.  The reductions (step-size sums, energies,
+ * and stencil arithmetic; MM_F32X2: double arrays, double-float arithmetic
+ * (see the enum).  The reductions (step-size sums, energies,
  * averages) are combined across CTAs in double and the step size is chosen in
  * double.  Within a CTA the MM_FP64 path accumulates in double; the MM_FP32
  * path adds every per-cell product exactly (an FMA-split product) into a
  * compensated float pair (about 46 significant bits), which mm_min_inspect
- * lets callers check against their own double reduction.
+ * lets callers check against their own double reduction; the MM_F32X2 path
+ * accumulates in double-float pairs.
  * Two layouts of the y-z stage of the convolution.  Film layout (nz <= 4 and
  * the padded y-z plane of one x-frequency, about 3 * nz * 9/8 * Py complex
  * values, within 200 KiB of shared memory; e.g. 512 x 256 x 4 in FP64 or
@@ -402,7 +406,8 @@ MM_API int mm_kernel_times(mm_problem *prob, const void *m, const double Hext[3]
  * (zero at k = 0), max_i |m_i x H_i| / Ms at iterate k and the mm_status of
  * that minimisation.  m_k, m_prev, g_k, g_prev (host or device, nullable,
  * problem precision, [3][nz][ny][nx]) receive m_k, m_{k-1}, g_k = m_k x
- * (m_k x H_k) and g_{k-1} as the kernels hold them (m_prev, g_prev
+ * (m_k x H_k) and g_{k-1} as the kernels hold them (MM_F32X2: the
+ * double-float pairs rounded to double; m_prev, g_prev
  * meaningful for k >= 1).  Lets callers check the step-size sums against
  * their own reduction of the same data.  Synchronises `stream`.
  */

@@ -303,6 +303,22 @@ int mm_copy_user(void *dst, const void *src, size_t bytes, bool dst_dev, bool sr
     return MM_OK;
 }
 
+// The caller's m into iterate buffer 0: a copy in the problem's element
+// type, or for MM_F32X2 a conversion of the caller's doubles to double-word
+// pairs (host arrays pass through the input staging buffer).
+int mm_load_iterate(mm_problem *p, const void *m, bool mdev, cudaStream_t s)
+{
+    const size_t F = 3 * (size_t)p->g.N * p->esz;
+    if (p->precision != MM_F32X2) return mm_copy_user(p->mbuf[0], m, F, true, mdev, s);
+    const void *src = m;
+    if (!mdev) {
+        int rc = mm_copy_user(p->stage_in, m, F, true, false, s);
+        if (rc) return rc;
+        src = p->stage_in;
+    }
+    return mm_launch_iterate_in(p, p->mbuf[0], (const double *)src, 3 * p->g.N, s);
+}
+
 namespace {
 #define copy_user mm_copy_user
 
@@ -542,7 +558,7 @@ extern "C" int mm_minimize(mm_problem *p, void *m, const double Hext[3], const m
     const size_t F = 3 * (size_t)p->g.N * p->esz;
     const bool mdev = is_device_ptr(m);
     int rc;
-    if ((rc = copy_user(p->mbuf[0], m, F, true, mdev, s))) return rc;
+    if ((rc = mm_load_iterate(p, m, mdev, s))) return rc;
     if ((rc = mm_launch_init_state(p, Hext, opts, 1, s))) return rc;
     if ((rc = mm_launch_loop(p, s))) return rc;
     if ((rc = mm_launch_copy_result(p, mdev ? m : p->stage_out, s))) return rc;
@@ -571,7 +587,7 @@ extern "C" int mm_hysteresis_sweep(mm_problem *p, void *m, const double *H_list,
         if ((rc = dalloc(p, (void **)&p->rec_dev, sizeof(StepRecord) * (size_t)n))) { p->rec_cap = 0; return rc; }
         p->rec_cap = n;
     }
-    if ((rc = copy_user(p->mbuf[0], m, F, true, mdev, s))) return rc;
+    if ((rc = mm_load_iterate(p, m, mdev, s))) return rc;
     for (int i = start; i < n; ++i) {
         if ((rc = mm_launch_init_state(p, H_list + 3 * i, opts, i == start, s))) return rc;
         if ((rc = mm_launch_loop(p, s))) return rc;
@@ -608,9 +624,8 @@ extern "C" int mm_kernel_times(mm_problem *p, const void *m, const double Hext[3
     NvtxRange nvtx_("mm_kernel_times");
     if (!p || !m || !vec_ok(Hext) || reps < 1 || !ms_out || !names || !count) return MM_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t F = 3 * (size_t)p->g.N * p->esz;
     int rc;
-    if ((rc = copy_user(p->mbuf[0], m, F, true, is_device_ptr(m), s))) return rc;
+    if ((rc = mm_load_iterate(p, m, is_device_ptr(m), s))) return rc;
     mm_min_opts o = {0.0, 0.0, 1L << 40, MM_STEP_CAYLEY, 0.0, MM_TAU_ALTERNATE, 0.0};
     if ((rc = mm_launch_init_state(p, Hext, &o, 1, s))) return rc;
     rc = mm_kernel_stage_times(p, reps, ms_out, names, count, s);
@@ -635,7 +650,14 @@ extern "C" int mm_min_inspect(mm_problem *p, mm_min_state *out, void *m_k, void 
     for (int i = 0; i < 4; ++i) {
         if (!dst[i]) continue;
         const bool ddev = is_device_ptr(dst[i]);
-        int rc = copy_user(dst[i], src[i], F, ddev, true, s);
+        int rc;
+        if (p->precision == MM_F32X2) {   // double-word storage: converted to the caller's double
+            void *d = ddev ? dst[i] : p->stage_out;
+            rc = mm_launch_iterate_out(p, (double *)d, src[i], 3 * p->g.N, s);
+            if (!rc && !ddev) rc = copy_user(dst[i], p->stage_out, F, false, true, s);
+        } else {
+            rc = copy_user(dst[i], src[i], F, ddev, true, s);
+        }
         if (rc) return rc;
     }
     CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");

@@ -627,9 +627,7 @@ int sweep_streams(mm_batch *b, void *const *m_list, const double *H_list, int n,
     // problem stream to the caller's stream so that no work is left unordered
     int rc = MM_OK;
     for (size_t i = 0; i < P && rc == MM_OK; ++i) {
-        mm_problem *p = b->probs[i];
-        const size_t F = 3 * (size_t)p->g.N * p->esz;
-        rc = mm_copy_user(p->mbuf[0], m_list[i], F, true, mm_is_device_ptr(m_list[i]), b->streams[i]);
+        rc = mm_load_iterate(b->probs[i], m_list[i], mm_is_device_ptr(m_list[i]), b->streams[i]);
     }
     for (int j = start; j < n && rc == MM_OK; ++j)
         for (size_t i = 0; i < P && rc == MM_OK; ++i) {
@@ -707,9 +705,7 @@ int sweep_grouped(mm_batch *b, void *const *m_list, const double *H_list, int n,
     }
     int rc = MM_OK;
     for (size_t i = 0; i < P && rc == MM_OK; ++i) {
-        mm_problem *p = b->probs[i];
-        const size_t F = 3 * (size_t)p->g.N * p->esz;
-        rc = mm_copy_user(p->mbuf[0], m_list[i], F, true, mm_is_device_ptr(m_list[i]), s);
+        rc = mm_load_iterate(b->probs[i], m_list[i], mm_is_device_ptr(m_list[i]), s);
     }
     // the whole sweep call: one graph launch
     if (rc == MM_OK && (e = cudaGraphLaunch(b->exec, s))) { mm_set_cuda_error(e, "cudaGraphLaunch(batch)"); rc = MM_ERR_CUDA; }

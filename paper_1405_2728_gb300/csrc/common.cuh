@@ -192,15 +192,23 @@ template <typename T> __host__ __device__ __forceinline__ T pick(double d, float
 // Field evaluation modes of the x-inverse/local kernel
 enum { MODE_HEFF = 0, MODE_ENERGY = 1, MODE_MIN = 2 };
 
-// T: element type of the fields m, H, g and of the local terms (double or
-// float); F: arithmetic type of the FFTs and the convolution, whose complex
-// values fill the spectrum buffers and the tensor (T itself, or dfloat for
-// MM_F32X2)
+// Element type of the caller's arrays for fields stored as T: T itself,
+// double for double-word storage (the ABI's arrays of an MM_F32X2 problem
+// are double; its iterates are kept as float pairs)
+template <typename T> struct io_of { typedef T type; };
+template <> struct io_of<dfloat> { typedef double type; };
+
+// T: element type of the minimiser's fields m and g and of the local terms
+// (double, float, or dfloat for MM_F32X2); F: arithmetic type of the FFTs and
+// the convolution, whose complex values fill the spectrum buffers and the
+// tensor; IO: the caller's element type (m for MODE_HEFF/ENERGY, H, per-cell
+// material)
 template <typename T, typename F = T>
 struct FieldPtrs {
     typedef typename cvec<F>::type V;
-    const T *m_src;        // field input for MODE_HEFF/ENERGY, or NULL (then mbuf by state)
-    T *H_out;              // MODE_HEFF output
+    typedef typename io_of<T>::type IO;
+    const IO *m_src;       // field input for MODE_HEFF/ENERGY, or NULL (then mbuf by state)
+    IO *H_out;             // MODE_HEFF output
     T *mbuf[2];            // minimiser iterate buffers
     T *gbuf[2];            // projected-gradient buffers
     V *W;                  // spectrum [C][nz][ny][3] (x-frequency slowest, component fastest)
@@ -211,8 +219,8 @@ struct FieldPtrs {
     const V *tw_px;        // exp(-2 pi i t/Px), t < Px
     const V *tw_py;        // exp(-2 pi i t/Py), t < Py
     const V *tw_pz;        // exp(-2 pi i t/Pz), t < Pz
-    const T *Kc;           // per-cell K or NULL
-    const T *uc;           // per-cell axis [3][N] or NULL
+    const IO *Kc;          // per-cell K or NULL
+    const IO *uc;          // per-cell axis [3][N] or NULL
     double *partials;      // [nblocks][RED_NSLOT]
     MinState *st;          // minimiser state (MODE_MIN and updates)
     unsigned *counter;     // CTAs of the current x-inverse launch that have finished (reset by the last)
@@ -307,7 +315,12 @@ int mm_autotune(mm_problem *p, const int *tys, int nty, const int *rbs, int nrb,
 int mm_launch_twiddles(mm_problem *p, cudaStream_t s);
 int mm_launch_field(mm_problem *p, const void *m, void *H, const double *hext, int mode, cudaStream_t s,
                     double hscale = 1.0);
+// double values into the problem's material type (per-cell K and axes:
+// float for MM_FP32, else double)
 int mm_launch_convert(mm_problem *p, void *dst, const double *src, long n, cudaStream_t s);
+// MM_F32X2 only: the caller's double values into double-word iterate storage, and back
+int mm_launch_iterate_in(mm_problem *p, void *dst, const double *src, long n, cudaStream_t s);
+int mm_launch_iterate_out(mm_problem *p, double *dst, const void *src, long n, cudaStream_t s);
 int mm_rebuild_graph(mm_problem *p);
 // implemented in bulk.cu: the three y-z passes of the bulk layout (pass -1:
 // all three in order; 0, 1, 2: only that one)
@@ -333,5 +346,7 @@ int mm_sm_count();
 // CTAs for n, at most `per_sm` resident CTAs on every SM of the device
 int mm_grid_for(long n, int threads, int per_sm);
 int mm_copy_user(void *dst, const void *src, size_t bytes, bool dst_dev, bool src_dev, cudaStream_t s);
+// the caller's m (host or device, the ABI's element type) into iterate buffer 0
+int mm_load_iterate(mm_problem *p, const void *m, bool mdev, cudaStream_t s);
 // error bookkeeping (api.cu)
 void mm_set_cuda_error(cudaError_t e, const char *where);

@@ -5,6 +5,8 @@
 // many problems), so both run the same arithmetic.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "fft.cuh"
 
@@ -32,6 +34,17 @@ template <> __device__ __forceinline__ dcomplex ld_cg(const dcomplex *p)
 // a value of the FFT arithmetic F read back in the field type T
 template <typename T, typename F> __device__ __forceinline__ T to_field(F v) { return (T)v; }
 template <> __device__ __forceinline__ double to_field<double, dfloat>(dfloat v) { return df_to_double(v); }
+// a caller's value (double for double-word fields) in the field type T, and back
+template <typename T> __device__ __forceinline__ T from_io(typename io_of<T>::type v) { return (T)v; }
+template <typename T> __device__ __forceinline__ typename io_of<T>::type to_io(T v) { return v; }
+template <> __device__ __forceinline__ double to_io<dfloat>(dfloat v) { return df_to_double(v); }
+// 1/sqrt(x) in the field type (the double and float steps divide by sqrt)
+template <typename T> __device__ __forceinline__ T inv_sqrt(T x) { return (T)1 / sqrt(x); }
+template <> __device__ __forceinline__ dfloat inv_sqrt<dfloat>(dfloat x) { return df_rsqrt(x); }
+// 1/|m| of the renormalisation after a midpoint step (float: the fast
+// reciprocal square root, ~2 ulp; double-word: one Newton step, ~2^-47)
+__device__ __forceinline__ float renorm_scale(float s) { return rsqrtf(s); }
+__device__ __forceinline__ dfloat renorm_scale(dfloat s) { return df_rsqrt(s); }
 
 // real element x of a padded complex row holding Px reals
 template <typename T, typename V> __device__ __forceinline__ T &rel(V *row, int x)
@@ -91,7 +104,9 @@ __device__ __forceinline__ void xfwd_body(const Geom &g, const FieldPtrs<T, F> &
     V *tw = S + 3 * TY * g.rsx;  // Px twiddles exp(-2 pi i t / Px)
     for (int i = tt; i < Px; i += nth) tw[i] = P.tw_px[i];
 
-    const T *src;
+    typedef typename io_of<T>::type IO;
+    const T *src = nullptr;        // minimiser mode: the iterate buffers
+    const IO *src_io = nullptr;    // otherwise the caller's m
     T *dst = nullptr;
     const T *gp = nullptr;
     T tau = 0;
@@ -110,7 +125,7 @@ __device__ __forceinline__ void xfwd_body(const Geom &g, const FieldPtrs<T, F> &
             src = cur ? P.mbuf[1] : P.mbuf[0];
         }
     } else {
-        src = P.m_src;
+        src_io = P.m_src;
     }
     // load (and step) the tile; row (c, yl) holds Px reals
 #pragma unroll(sizeof(T) == 4 ? 2 : 1)
@@ -119,26 +134,31 @@ __device__ __forceinline__ void xfwd_body(const Geom &g, const FieldPtrs<T, F> &
         T m0 = 0, m1 = 0, m2 = 0;
         if (y < ny) {
             const long n = ((long)z * ny + y) * nx + x;
-            m0 = __ldg(src + n); m1 = __ldg(src + N + n); m2 = __ldg(src + 2 * N + n);
+            if constexpr (MIN) {
+                m0 = ldg(src + n); m1 = ldg(src + N + n); m2 = ldg(src + 2 * N + n);
+            } else {
+                m0 = from_io<T>(ldg(src_io + n)); m1 = from_io<T>(ldg(src_io + N + n));
+                m2 = from_io<T>(ldg(src_io + 2 * N + n));
+            }
             if (MIN && dst) {
-                const T g0 = __ldg(gp + n), g1 = __ldg(gp + N + n), g2 = __ldg(gp + 2 * N + n);
+                const T g0 = ldg(gp + n), g1 = ldg(gp + N + n), g2 = ldg(gp + 2 * N + n);
                 if (step_kind == MM_STEP_CAYLEY) {
                     const T q = (T)0.25 * tau * tau * (g0 * g0 + g1 * g1 + g2 * g2);
                     const T a = (T)1 - q, inv = (T)1 / ((T)1 + q);
                     m0 = (a * m0 - tau * g0) * inv;
                     m1 = (a * m1 - tau * g1) * inv;
                     m2 = (a * m2 - tau * g2) * inv;
-                    if (sizeof(T) == 4) {
-                        // float path only: the closed form keeps |m| = 1 exactly in
-                        // exact arithmetic; in float its rounding drifts ~1e-7 per
-                        // step, so the float path renormalises (the double path keeps
-                        // the pure midpoint form, drift ~1e-16 per step)
-                        const T r = rsqrtf((float)(m0 * m0 + m1 * m1 + m2 * m2));
+                    if constexpr (!std::is_same<T, double>::value) {
+                        // the closed form keeps |m| = 1 exactly in exact arithmetic;
+                        // its rounding drifts ~1e-7 per step in float and ~1e-14 in
+                        // double-word arithmetic, so those paths renormalise (the
+                        // double path keeps the pure midpoint form, ~1e-16 per step)
+                        const T r = renorm_scale(m0 * m0 + m1 * m1 + m2 * m2);
                         m0 *= r; m1 *= r; m2 *= r;
                     }
                 } else {
                     m0 -= tau * g0; m1 -= tau * g1; m2 -= tau * g2;
-                    const T inv = (T)1 / sqrt(m0 * m0 + m1 * m1 + m2 * m2);
+                    const T inv = inv_sqrt(m0 * m0 + m1 * m1 + m2 * m2);
                     m0 *= inv; m1 *= inv; m2 *= inv;
                 }
                 dst[n] = m0; dst[N + n] = m1; dst[2 * N + n] = m2;
@@ -162,22 +182,30 @@ __device__ __forceinline__ void xfwd_body(const Geom &g, const FieldPtrs<T, F> &
         fft_row<false, true, false, 2, LX>(S + (act ? row : 0) * g.rsx, g.Hx, g.lhx, j, tw, act);
     }
 
-    // unpack to the real-input spectrum X[k], k = 0..Hx, and store transposed
-    const int Hx = g.Hx, C = g.C;
-    for (int e = tt; e < TY * 3 * C; e += nth) {
+    // unpack to the real-input spectrum X[k], k = 0..Hx, and store transposed.
+    // With sum = Z[k] + Z*[Hx-k], dif = Z[k] - Z*[Hx-k] and w = exp(-2 pi i k / Px):
+    // X[k] = (sum - i w dif) / 2 and, from the same two values (w^Hx = -1),
+    // X[Hx-k] = (sum* - i (w dif)*) / 2; one item per pair k = 0..Hx/2.
+    const int Hx = g.Hx, hh = Hx >> 1;
+    for (int e = tt; e < TY * 3 * (hh + 1); e += nth) {
         const int c = e % 3, rest = e / 3, yl = rest & (TY - 1), k = rest >> g.ltyf;
         const int y = y0 + yl;
         const V *row = S + (c * TY + yl) * g.rsx;
-        const V Zk = row[spos<V>(k == Hx ? 0 : k)];
+        const V Zk = row[spos<V>(k)];
         const V Zm = cconj(row[spos<V>(k == 0 ? 0 : Hx - k)]);
-        const V w = tw[k];
         const V sum = cadd(Zk, Zm), dif = csub(Zk, Zm);
-        // X = (sum - i w dif) / 2
-        const V wd = cmul(w, dif);
-        V X;
-        X.x = F(0.5) * (sum.x + wd.y);
-        X.y = F(0.5) * (sum.y - wd.x);
-        if (y < ny) P.W[(((long)k * g.nz + z) * ny + y) * 3 + c] = X;
+        const V wd = cmul(tw[k], dif);
+        if (y < ny) {
+            V X;
+            X.x = F(0.5) * (sum.x + wd.y);
+            X.y = F(0.5) * (sum.y - wd.x);
+            P.W[(((long)k * g.nz + z) * ny + y) * 3 + c] = X;
+            if (Hx - k != k) {
+                X.x = F(0.5) * (sum.x - wd.y);
+                X.y = F(0.5) * (-sum.y - wd.x);
+                P.W[(((long)(Hx - k) * g.nz + z) * ny + y) * 3 + c] = X;
+            }
+        }
     }
 }
 
@@ -374,6 +402,30 @@ template <> struct Acc<float> {
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// double-word accumulator of the MM_F32X2 fields: per-cell products and sums
+// in double-word arithmetic (relative rounding a few units of 2^-48 per
+// operation), converted to double for the sums across CTAs
+template <> struct Acc<dfloat> {
+    dfloat v;
+    __device__ __forceinline__ void zero() { v = dfloat(0.0f, 0.0f); }
+    __device__ __forceinline__ void add(dfloat x) { v = v + x; }
+    __device__ __forceinline__ void add_prod(dfloat a, dfloat b) { v = v + a * b; }
+    __device__ __forceinline__ void add(const Acc &o) { v = v + o.v; }
+    __device__ __forceinline__ void maxv(dfloat x)
+    {
+        if (x.hi > v.hi || (x.hi == v.hi && x.lo > v.lo)) v = x;
+    }
+    __device__ __forceinline__ void maxv(const Acc &o) { maxv(o.v); }
+    __device__ __forceinline__ Acc shfl_down(int o) const
+    {
+        Acc r;
+        r.v.hi = __shfl_down_sync(0xffffffffu, v.hi, o);
+        r.v.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
+        return r;
+    }
+    __device__ __forceinline__ double value() const { return df_to_double(v); }
+};
+
 __device__ __forceinline__ unsigned long long globaltimer_ns()
 {
     unsigned long long t;
@@ -480,7 +532,10 @@ __device__ __forceinline__ void xinv_body(const Geom &g, const FieldPtrs<T, F> &
     MinState *st = P.st;
     long k = 0;
     int cur = 0;
-    const T *m;
+    typedef typename io_of<T>::type IO;
+    constexpr bool FROM_T = MODE == MODE_MIN || std::is_same<T, IO>::value;
+    const T *m = nullptr;       // m in the field type (the iterate, or the caller's m of that type)
+    const IO *mio = nullptr;    // the caller's m when it is of another type (converted per load)
     const T *mp = nullptr, *gq = nullptr;
     if (MODE == MODE_MIN) {
         k = st->k;
@@ -488,9 +543,15 @@ __device__ __forceinline__ void xinv_body(const Geom &g, const FieldPtrs<T, F> &
         m = cur ? P.mbuf[1] : P.mbuf[0];
         mp = cur ? P.mbuf[0] : P.mbuf[1];
         gq = (k & 1) ? P.gbuf[0] : P.gbuf[1];  // g_{k-1}
-    } else {
+    } else if constexpr (std::is_same<T, IO>::value) {
         m = P.m_src;
+    } else {
+        mio = P.m_src;
     }
+    auto mval = [&](long i) -> T {
+        if constexpr (FROM_T) return m[i];
+        else return from_io<T>(mio[i]);
+    };
     // the float kernel stages the local terms' inputs -- m on planes z-1, z,
     // z+1 (rows y0-1 .. y0+TY on its own plane), m_{k-1} and g_{k-1} -- with
     // cp.async now; they arrive while the inverse x-FFT runs
@@ -513,10 +574,13 @@ __device__ __forceinline__ void xinv_body(const Geom &g, const FieldPtrs<T, F> &
     }
     cp_async_commit();
 
-    // complex-to-real preprocessing: Z[k] = (X[k] + X*[Hx-k]) + i conj(w^k) (X[k] - X*[Hx-k]);
-    // the spectrum loads of PF elements per thread are issued before any is used
+    // complex-to-real preprocessing: Z[k] = (X[k] + X*[Hx-k]) + i conj(w^k) (X[k] - X*[Hx-k]).
+    // With sum and dif the two brackets and t = conj(w^k) dif, Z[k] = sum + i t and
+    // (w^Hx = -1) Z[Hx-k] = sum* + i t*: one item per pair k = 0..Hx/2 loads X[k] and
+    // X[Hx-k] once.  The loads of PF items per thread are issued before any is used.
     constexpr int PF = sizeof(V) == 8 ? 8 : 4;
-    const int nel = TY * 3 * Hx;
+    const int hh = Hx >> 1;
+    const int nel = TY * 3 * (hh + 1);
     const long strideK = (long)3 * nz * ny;
     for (int g0 = 0; g0 < nel; g0 += PF * nth) {  // trip count uniform over the CTA (barrier inside)
         const int e0 = g0 + tt;
@@ -544,10 +608,16 @@ __device__ __forceinline__ void xinv_body(const Geom &g, const FieldPtrs<T, F> &
             const V Xk = xa[i], Xm = cconj(xb[i]);
             const V sum = cadd(Xk, Xm), dif = csub(Xk, Xm);
             const V t = cmulc(dif, tw[kk]);  // conj(w^k) dif
+            V *row = S + (c * TY + yl) * g.rsx;
             V Z;
             Z.x = sum.x - t.y;
             Z.y = sum.y + t.x;
-            S[(c * TY + yl) * g.rsx + spos<V>(kk)] = Z;
+            row[spos<V>(kk)] = Z;
+            if (kk != 0 && Hx - kk != kk) {
+                Z.x = sum.x + t.y;
+                Z.y = t.x - sum.y;
+                row[spos<V>(Hx - kk)] = Z;
+            }
         }
     }
     __syncthreads();
@@ -599,19 +669,23 @@ __device__ __forceinline__ void xinv_body(const Geom &g, const FieldPtrs<T, F> &
             if (z > 0)      { const T *q = rz + oZm; e0 += cz * (q[0] - m0); e1 += cz * (q[ct] - m1); e2 += cz * (q[2 * ct] - m2); }
             if (z < nz - 1) { const T *q = rz + oZp; e0 += cz * (q[0] - m0); e1 += cz * (q[ct] - m1); e2 += cz * (q[2 * ct] - m2); }
         } else {
-            m0 = __ldg(m + n); m1 = __ldg(m + N + n); m2 = __ldg(m + 2 * N + n);
-            if (x > 0)      { e0 += cx * (m[n - 1] - m0);  e1 += cx * (m[N + n - 1] - m1);  e2 += cx * (m[2 * N + n - 1] - m2); }
-            if (x < nx - 1) { e0 += cx * (m[n + 1] - m0);  e1 += cx * (m[N + n + 1] - m1);  e2 += cx * (m[2 * N + n + 1] - m2); }
-            if (y > 0)      { e0 += cy * (m[n - nx] - m0); e1 += cy * (m[N + n - nx] - m1); e2 += cy * (m[2 * N + n - nx] - m2); }
-            if (y < ny - 1) { e0 += cy * (m[n + nx] - m0); e1 += cy * (m[N + n + nx] - m1); e2 += cy * (m[2 * N + n + nx] - m2); }
+            if constexpr (FROM_T) {
+                m0 = ldg(m + n); m1 = ldg(m + N + n); m2 = ldg(m + 2 * N + n);
+            } else {
+                m0 = from_io<T>(ldg(mio + n)); m1 = from_io<T>(ldg(mio + N + n)); m2 = from_io<T>(ldg(mio + 2 * N + n));
+            }
+            if (x > 0)      { e0 += cx * (mval(n - 1) - m0);  e1 += cx * (mval(N + n - 1) - m1);  e2 += cx * (mval(2 * N + n - 1) - m2); }
+            if (x < nx - 1) { e0 += cx * (mval(n + 1) - m0);  e1 += cx * (mval(N + n + 1) - m1);  e2 += cx * (mval(2 * N + n + 1) - m2); }
+            if (y > 0)      { e0 += cy * (mval(n - nx) - m0); e1 += cy * (mval(N + n - nx) - m1); e2 += cy * (mval(2 * N + n - nx) - m2); }
+            if (y < ny - 1) { e0 += cy * (mval(n + nx) - m0); e1 += cy * (mval(N + n + nx) - m1); e2 += cy * (mval(2 * N + n + nx) - m2); }
             const long sxy = (long)nx * ny;
-            if (z > 0)      { e0 += cz * (m[n - sxy] - m0); e1 += cz * (m[N + n - sxy] - m1); e2 += cz * (m[2 * N + n - sxy] - m2); }
-            if (z < nz - 1) { e0 += cz * (m[n + sxy] - m0); e1 += cz * (m[N + n + sxy] - m1); e2 += cz * (m[2 * N + n + sxy] - m2); }
+            if (z > 0)      { e0 += cz * (mval(n - sxy) - m0); e1 += cz * (mval(N + n - sxy) - m1); e2 += cz * (mval(2 * N + n - sxy) - m2); }
+            if (z < nz - 1) { e0 += cz * (mval(n + sxy) - m0); e1 += cz * (mval(N + n + sxy) - m1); e2 += cz * (mval(2 * N + n + sxy) - m2); }
         }
         // uniaxial anisotropy
-        const T Kv = P.Kc ? P.Kc[n] : Kuni;
+        const T Kv = P.Kc ? from_io<T>(P.Kc[n]) : Kuni;
         T u0, u1, u2;
-        if (P.uc) { u0 = P.uc[n]; u1 = P.uc[N + n]; u2 = P.uc[2 * N + n]; }
+        if (P.uc) { u0 = from_io<T>(P.uc[n]); u1 = from_io<T>(P.uc[N + n]); u2 = from_io<T>(P.uc[2 * N + n]); }
         else { u0 = ux; u1 = uy; u2 = uz; }
         const T mu = m0 * u0 + m1 * u1 + m2 * u2;
         const T ka = can * Kv * mu;
@@ -619,7 +693,7 @@ __device__ __forceinline__ void xinv_body(const Geom &g, const FieldPtrs<T, F> &
         const T H1 = d1 + e1 + ka * u1 + he1;
         const T H2 = d2 + e2 + ka * u2 + he2;
         if (MODE == MODE_HEFF) {
-            P.H_out[n] = hs * H0; P.H_out[N + n] = hs * H1; P.H_out[2 * N + n] = hs * H2;
+            P.H_out[n] = to_io(hs * H0); P.H_out[N + n] = to_io(hs * H1); P.H_out[2 * N + n] = to_io(hs * H2);
             continue;
         }
         red[SL_MX].add(m0); red[SL_MY].add(m1); red[SL_MZ].add(m2);
@@ -742,7 +816,8 @@ template <typename T, typename F = T> FieldPtrs<T, F> make_ptrs(mm_problem *p)
     P.gbuf[0] = (T *)p->gbuf[0]; P.gbuf[1] = (T *)p->gbuf[1];
     P.W = (V *)p->W; P.W2 = (V *)p->W2; P.Nhat = (const F *)p->Nhat;
     P.tw_px = (const V *)p->tw_px; P.tw_py = (const V *)p->tw_py; P.tw_pz = (const V *)p->tw_pz;
-    P.Kc = (const T *)p->Kc; P.uc = (const T *)p->uc;
+    typedef typename io_of<T>::type IO;
+    P.Kc = (const IO *)p->Kc; P.uc = (const IO *)p->uc;
     P.partials = p->partials; P.st = p->st; P.counter = p->counter;
     P.hscale = 1.0;
     return P;

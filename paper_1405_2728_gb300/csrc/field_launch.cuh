@@ -69,12 +69,16 @@ cudaError_t launch_yz_any(const Geom &g, const FieldPtrs<T, F> &P, cudaStream_t 
     }
 }
 
+// the bulk layout's passes exist for double and float (double-word problems
+// are film-layout only: the planner refuses bulk grids for them)
+template <typename T, typename F>
+constexpr bool has_bulk = std::is_same<T, F>::value && !std::is_same<F, dfloat>::value;
+
 // the y-z stage: the film kernel, or the three passes of the bulk layout
-// (double-float problems are film-layout only: the planner refuses bulk grids for them)
 template <typename T, typename F>
 cudaError_t launch_conv(const Geom &g, const FieldPtrs<T, F> &P, cudaStream_t s)
 {
-    if constexpr (std::is_same<T, F>::value) {
+    if constexpr (has_bulk<T, F>) {
         if (g.bulk) return mm_bulk_conv(g, P, s, -1);
     }
     return launch_yz_any<T, F>(g, P, s);
@@ -130,9 +134,10 @@ template <typename T, typename F> cudaError_t autotune_t(mm_problem *p, const in
                                              cudaStream_t s)
 {
     Geom g = p->g;
+    typedef typename io_of<T>::type IO;
     FieldPtrs<T, F> P = make_ptrs<T, F>(p);
-    P.m_src = (const T *)p->mbuf[0];
-    P.H_out = (T *)p->gbuf[0];
+    P.m_src = (const IO *)p->mbuf[0];
+    P.H_out = (IO *)p->gbuf[0];
     cudaEvent_t a, b;
     cudaError_t e;
     // a minimiser state past its first iteration, so that the step and the
@@ -202,9 +207,10 @@ cudaError_t heff_chain_t(mm_problem *p, const void *m, void *H, const double *he
                          double hscale)
 {
     const Geom &g = p->g;
+    typedef typename io_of<T>::type IO;
     FieldPtrs<T, F> P = make_ptrs<T, F>(p);
-    P.m_src = (const T *)m;
-    P.H_out = (T *)H;
+    P.m_src = (const IO *)m;
+    P.H_out = (IO *)H;
     P.hscale = hscale;
     cudaError_t e = launch_xfwd<T, F, false>(g, P, s);
     if (e) return e;
@@ -241,7 +247,7 @@ cudaError_t stage_times_t(mm_problem *p, int reps, double *ms, cudaStream_t s)
         launch_xfwd<T, F, true>(g, P, s);
         cudaEventRecord(ev[i++], s);
         if (g.bulk) {
-            if constexpr (std::is_same<T, F>::value) {
+            if constexpr (has_bulk<T, F>) {
                 for (int pass = 0; pass < 3; ++pass) {
                     mm_bulk_conv(g, P, s, pass);
                     cudaEventRecord(ev[i++], s);

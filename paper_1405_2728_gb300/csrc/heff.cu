@@ -29,7 +29,8 @@
 // Sums are accumulated in double on the double path.  On the float path each
 // per-cell product enters its sum exactly (TwoProduct with one FMA) and the
 // sums are compensated float pairs (TwoSum, Knuth), about 46 significant
-// bits; partial sums are always combined across CTAs in double.
+// bits; the double-word path (MM_F32X2) sums in double-word arithmetic.
+// Partial sums are always combined across CTAs in double.
 #include <cstdio>
 #include <cstring>
 #include <type_traits>
@@ -70,12 +71,20 @@ __global__ void k_record(const MinState *st, StepRecord *rec, int step)
     rec[step] = r;
 }
 
+// the current iterate, in the caller's element type
 template <typename T>
-__global__ void k_copy_result(const MinState *st, const T *b0, const T *b1, T *dst, long n3)
+__global__ void k_copy_result(const MinState *st, const T *b0, const T *b1, typename io_of<T>::type *dst, long n3)
 {
     const T *src = (st->base ^ (int)(st->k & 1)) ? b1 : b0;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n3; i += (long)gridDim.x * blockDim.x)
-        dst[i] = src[i];
+        dst[i] = to_io(src[i]);
+}
+
+// double-word fields to the caller's double
+__global__ void k_dfloat_to_double(double *dst, const dfloat *src, long n)
+{
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        dst[i] = df_to_double(src[i]);
 }
 
 template <typename T>
@@ -202,7 +211,10 @@ int mm_launch_copy_result(mm_problem *p, void *dst, cudaStream_t s)
 {
     const long n3 = 3 * p->g.N;
     const int blocks = mm_grid_for(n3, 256, 8);
-    if (mm_double_fields(p))
+    if (p->precision == MM_F32X2)
+        k_copy_result<dfloat><<<blocks, 256, 0, s>>>(p->st, (const dfloat *)p->mbuf[0],
+                                                    (const dfloat *)p->mbuf[1], (double *)dst, n3);
+    else if (p->precision == MM_FP64)
         k_copy_result<double><<<blocks, 256, 0, s>>>(p->st, (const double *)p->mbuf[0],
                                                     (const double *)p->mbuf[1], (double *)dst, n3);
     else
@@ -226,6 +238,24 @@ int mm_launch_twiddles(mm_problem *p, cudaStream_t s)
     }
     cudaError_t e = cudaGetLastError();
     if (e) { mm_set_cuda_error(e, "k_twiddle"); return MM_ERR_CUDA; }
+    return MM_OK;
+}
+
+int mm_launch_iterate_in(mm_problem *p, void *dst, const double *src, long n, cudaStream_t s)
+{
+    if (p->precision != MM_F32X2) return MM_ERR_ARG;   // the other precisions store the caller's type
+    k_convert<dfloat><<<mm_grid_for(n, 256, 8), 256, 0, s>>>((dfloat *)dst, src, n);
+    cudaError_t e = cudaGetLastError();
+    if (e) { mm_set_cuda_error(e, "k_convert"); return MM_ERR_CUDA; }
+    return MM_OK;
+}
+
+int mm_launch_iterate_out(mm_problem *p, double *dst, const void *src, long n, cudaStream_t s)
+{
+    if (p->precision != MM_F32X2) return MM_ERR_ARG;
+    k_dfloat_to_double<<<mm_grid_for(n, 256, 8), 256, 0, s>>>(dst, (const dfloat *)src, n);
+    cudaError_t e = cudaGetLastError();
+    if (e) { mm_set_cuda_error(e, "k_dfloat_to_double"); return MM_ERR_CUDA; }
     return MM_OK;
 }
 

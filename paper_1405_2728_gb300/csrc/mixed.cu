@@ -20,25 +20,35 @@
 
 namespace {
 
+// element conversions between the iterate types of the two problems
+__device__ __forceinline__ void put(float &d, double v) { d = (float)v; }
+__device__ __forceinline__ void put(double &d, float v) { d = v; }
+__device__ __forceinline__ void put(float &d, dfloat v) { d = __fadd_rn(v.hi, v.lo); }  // nearest float to hi + lo
+__device__ __forceinline__ void put(dfloat &d, float v) { d = dfloat(v, 0.0f); }
+
 template <typename S, typename D>
 __global__ void k_transfer(const MinState *st, const S *b0, const S *b1, D *dst, long n3)
 {
     const S *src = (st->base ^ (int)(st->k & 1)) ? b1 : b0;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n3; i += (long)gridDim.x * blockDim.x)
-        dst[i] = (D)src[i];
+        put(dst[i], src[i]);
 }
 
-// current iterate of `from` -> iterate 0 of `to` (converted)
+template <typename S, typename D> void launch_transfer(mm_problem *from, mm_problem *to, long n3, cudaStream_t s)
+{
+    k_transfer<S, D><<<mm_grid_for(n3, 256, 8), 256, 0, s>>>(from->st, (const S *)from->mbuf[0],
+                                                            (const S *)from->mbuf[1], (D *)to->mbuf[0], n3);
+}
+
+// current iterate of `from` -> iterate 0 of `to` (converted): the float
+// problem and the double (or double-word) one, in either direction
 int transfer(mm_problem *from, mm_problem *to, cudaStream_t s)
 {
     const long n3 = 3 * from->g.N;
-    const int blocks = mm_grid_for(n3, 256, 8);
-    if (mm_double_fields(from))
-        k_transfer<double, float><<<blocks, 256, 0, s>>>(from->st, (const double *)from->mbuf[0],
-                                                         (const double *)from->mbuf[1], (float *)to->mbuf[0], n3);
-    else
-        k_transfer<float, double><<<blocks, 256, 0, s>>>(from->st, (const float *)from->mbuf[0],
-                                                         (const float *)from->mbuf[1], (double *)to->mbuf[0], n3);
+    if (from->precision == MM_FP64) launch_transfer<double, float>(from, to, n3, s);
+    else if (from->precision == MM_F32X2) launch_transfer<dfloat, float>(from, to, n3, s);
+    else if (to->precision == MM_FP64) launch_transfer<float, double>(from, to, n3, s);
+    else launch_transfer<float, dfloat>(from, to, n3, s);
     cudaError_t e = cudaGetLastError();
     if (e) { mm_set_cuda_error(e, "k_transfer"); return MM_ERR_CUDA; }
     return MM_OK;
@@ -107,7 +117,7 @@ extern "C" MM_API int mm_hysteresis_sweep_mixed(mm_problem *lo, mm_problem *hi, 
     const bool mdev = mm_is_device_ptr(m);
     int rc;
     if ((rc = ensure_records(lo, n)) || (rc = ensure_records(hi, n))) return rc;
-    if ((rc = mm_copy_user(hi->mbuf[0], m, F, true, mdev, s))) return rc;
+    if ((rc = mm_load_iterate(hi, m, mdev, s))) return rc;
     // the double problem's current iterate is now buffer 0 (base 0, k 0)
     if ((rc = mm_launch_init_state(hi, H_list + 3 * start, opts_hi, 1, s))) return rc;
     for (int j = start; j < n; ++j) {
