@@ -410,6 +410,73 @@ def run_mixed_loop(args, w, dev):
     return 0
 
 
+def run_precision_compare(args, w, dev):
+    """The precision extension's comparison: one whole loop of the workload's
+    sweep (the first --values field values) in FP32 and in FP64 from the same
+    seeded start, each timed with CUDA events, and every FP32 result (<m>,
+    energy per field value, the switching field) compared with the FP64 one."""
+    import torch
+    from paper_1405_2728_gb300 import inputs, mm
+    grid = mm.make_grid(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz)
+    mat = mm.make_material(w.Ms, w.A, w.K, K_cell=w.K_cell, u_cell=w.u_cell)
+    F = w.fields()
+    if args.values:
+        F = F[: args.values]
+    opts = mm.make_opts(tol=w.tol, max_iter=args.max_iter)
+    stream = torch.cuda.current_stream(dev)
+    runs = {}
+    sampler = ClockSampler(int(str(dev).split(":")[-1] or 0))
+    with sampler:
+        for name, prec, dt in (("fp64", mm.MM_FP64, torch.float64), ("fp32", mm.MM_FP32, torch.float32)):
+            prob = mm.mm_setup_geometry(grid, mat, prec)
+            m = torch.from_numpy(w.initial_m()).to(device=dev, dtype=dt).contiguous()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            st, mavg, res = mm.mm_hysteresis_sweep(prob, m, F, opts=opts, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            runs[name] = {"sec": a.elapsed_time(b) / 1e3, "mavg": mavg, "res": res, "status": int(st)}
+            prob.close()
+    hhat = F[int(np.argmax(np.linalg.norm(F, axis=1)))]
+    hhat = hhat / np.linalg.norm(hhat)
+    h = (F @ hhat) * inputs.MU0
+    top = int(np.argmax(h))                  # ramp 0 -> +max, then +max -> -max
+
+    def switching(mv):
+        p = mv @ hhat
+        idx = [i for i in range(top + 1, len(h)) if h[i] < 0 and p[i] < 0]
+        return float(h[idx[0]]) if idx else None
+
+    def remanence(mv):
+        idx = [i for i in range(top + 1, len(h)) if abs(h[i]) < 1e-12]
+        return float(mv[idx[0]] @ hhat) if idx else None
+
+    d = np.abs(runs["fp32"]["mavg"] - runs["fp64"]["mavg"]).max(axis=1)
+    e64 = np.array([r.energy for r in runs["fp64"]["res"]])
+    e32 = np.array([r.energy for r in runs["fp32"]["res"]])
+    de = np.abs(e32 - e64) / np.maximum(np.abs(e64), 1e-300)
+    out = {}
+    for name, r in runs.items():
+        ev = sum(x.heff_evals for x in r["res"])
+        out[name] = {"loop_time_s": r["sec"], "loop_evals": int(ev), "evals_per_s": ev / r["sec"],
+                     "converged_field_values": int(sum(x.converged for x in r["res"])), "status": r["status"],
+                     "H_sw_T": switching(r["mavg"]), "M_r": remanence(r["mavg"])}
+    line = {"metric": METRIC, "value": out["fp32"]["evals_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+            "warmup": 0, "ms_per_step": out["fp32"]["loop_time_s"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (compared with f64)", "data": "synthetic",
+            "config": {"workload": w.name, "cells": [w.nx, w.ny, w.nz], "precision": "fp32 vs fp64",
+                       "step": f"one loop of {len(F)} field values in each precision, tol {w.tol:g}"},
+            "fp64": out["fp64"], "fp32": out["fp32"],
+            "fp32_vs_fp64": {"max_abs_dmavg": float(d.max()), "median_abs_dmavg": float(np.median(d)),
+                             "values_within_1e-3": int((d <= 1e-3).sum()), "field_values": len(F),
+                             "max_rel_denergy": float(de.max()), "median_rel_denergy": float(np.median(de)),
+                             "loop_time_ratio_fp64_over_fp32": out["fp64"]["loop_time_s"] / out["fp32"]["loop_time_s"]},
+            "clocks": sampler.summary()}
+    print(json.dumps(line))
+    return 0
+
+
 def all_workloads(inputs):
     return {**inputs.WORKLOADS, **inputs.BULK_WORKLOADS}
 
@@ -417,11 +484,15 @@ def all_workloads(inputs):
 def run_batch(args, ws, rank, local, dev):
     """64 films of uneven size (inputs.batch_films), FP64, each with its own
     +-50 mT sweep in 2 mT steps.  A step is one field value for every film:
-    K field values for all 64 films in one mm_batch_sweep call (one graph
-    launch whose loop runs one grouped launch per kernel stage over every film
-    still running, each film walking its own field values), then the same K
-    field values film by film with mm_hysteresis_sweep for the sequential
-    comparison.  The L2 is flushed before each of the two timed calls."""
+    K field values for all 64 films in one mm_batch_sweep call, timed for each
+    way of running a batch -- the branch graph (the default: one graph launch,
+    an independent branch per film with its own nested minimiser loop), the
+    grouped launches (one graph launch, one grouped launch per kernel stage
+    over the films still running) and a stream per film -- against the same K
+    field values swept film by film with mm_hysteresis_sweep.  The sequential
+    sweeps run first and the grouped batch last, because making a grouped
+    batch harmonises the members' tiles.  The L2 is flushed before each timed
+    call."""
     import torch
     from paper_1405_2728_gb300 import inputs, mm
     films = inputs.batch_films(64)
@@ -432,71 +503,77 @@ def run_batch(args, ws, rank, local, dev):
     F = films[0].fields()
     opts = mm.make_opts(tol=films[0].tol, max_iter=200000)
     stream = torch.cuda.current_stream(dev)
-    batch = mm.mm_batch_create(probs)
-    ms_b = [torch.from_numpy(w.initial_m()).to(device=dev, dtype=tdt) for w in films]
-    ms_s = [m.clone() for m in ms_b]
     flush = torch.empty(int(256 * 2**20) // 4, dtype=torch.float32, device=dev)
+    K, W = args.steps, args.warmup
 
-    def batch_sweep(i0, k):
-        """field values i0 .. i0+k-1 for all films in one mm_batch_sweep call
-        (one graph launch: every film walks its own field values)"""
-        st, _, res = mm.mm_batch_sweep(batch, ms_b, F[: i0 + k], start=i0, opts=opts, stream=stream)
-        ev = sum(r[j].heff_evals for r in res for j in range(i0, i0 + k))
-        # per loop iteration three grouped stage kernels and the advance
-        # kernel; iterations = the largest total of evaluations of one film
-        iters = max(sum(r[j].heff_evals for j in range(i0, i0 + k)) for r in res)
-        return ev, 1 + 4 * iters
+    def fresh():
+        return [torch.from_numpy(w.initial_m()).to(device=dev, dtype=tdt) for w in films]
 
-    def seq_sweep(i0, k):
-        ev = 0
-        for p, m in zip(probs, ms_s):
-            st, _, res = mm.mm_hysteresis_sweep(p, m, F[: i0 + k], start=i0, opts=opts, stream=stream)
-            ev += sum(res[j].heff_evals for j in range(i0, i0 + k))
-        return ev
-
-    batch_sweep(0, args.warmup)
-    seq_sweep(0, args.warmup)
-    torch.cuda.synchronize()
-    K = args.steps
-    sampler = ClockSampler(local)
-    with sampler:
+    def timed(fn):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
         a.record(stream)
-        ev_b, launches = batch_sweep(args.warmup, K)
+        out = fn()
         b.record(stream)
         torch.cuda.synchronize()
-        t_b = a.elapsed_time(b)
-        flush.zero_()
-        a.record(stream)
-        ev_s = seq_sweep(args.warmup, K)
-        b.record(stream)
-        torch.cuda.synchronize()
-        t_s = a.elapsed_time(b)
+        return out, a.elapsed_time(b)
+
+    sampler = ClockSampler(local)
+    results = {}
+    with sampler:
+        ms = fresh()
+
+        def seq(i0, k):
+            ev = 0
+            for p, m in zip(probs, ms):
+                st, _, res = mm.mm_hysteresis_sweep(p, m, F[: i0 + k], start=i0, opts=opts, stream=stream)
+                ev += sum(res[j].heff_evals for j in range(i0, i0 + k))
+            return ev
+        seq(0, W)
+        ev_s, t_s = timed(lambda: seq(W, K))
+        for name, kind in (("branches", mm.MM_BATCH_BRANCHES), ("streams", mm.MM_BATCH_STREAMS),
+                           ("grouped", mm.MM_BATCH_GROUPED)):
+            batch = mm.mm_batch_create(probs, kind)
+            ms = fresh()
+
+            def bsweep(i0, k):
+                st, _, res = mm.mm_batch_sweep(batch, ms, F[: i0 + k], start=i0, opts=opts, stream=stream)
+                ev_f = [sum(r[j].heff_evals for j in range(i0, i0 + k)) for r in res]
+                if kind == mm.MM_BATCH_GROUPED:   # 3 grouped stage kernels and the advance kernel per iteration
+                    launches = 1 + 4 * max(ev_f)
+                else:                            # per film: 3 kernels per iteration, init and record per value
+                    launches = sum(3 * e + 2 * k for e in ev_f)
+                return sum(ev_f), launches
+            bsweep(0, W)
+            (ev_b, launches), t_b = timed(lambda: bsweep(W, K))
+            results[name] = {"value": ev_b / (t_b / 1e3), "unit": UNIT, "ms_per_step": t_b / K,
+                             "evals_per_step": ev_b / K, "speedup_vs_sequential": t_s / t_b,
+                             "gpu_launches": int(launches)}
+            batch.close()
     clocks = sampler.summary()
     if rank != 0:
         return 0
-    value = ev_b / (t_b / 1e3)
+    head = results["branches"]
     cells = [w.ncells for w in films]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
-        "ms_per_step": t_b / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+        "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == mm.MM_FP64 else "f32", "data": "synthetic",
         "config": {"workload": "batch64_films", "films": len(films), "cells_min_max_sum": [min(cells), max(cells), sum(cells)],
                    "precision": args.precision,
                    "step": "one field value of the +-50 mT / 2 mT sweep for all 64 films, tol 1e-5; the K timed "
                            "steps are one mm_batch_sweep call",
                    "l2": "flushed before each timed call (256 MiB write)",
-                   "parallelism": "one graph launch per sweep call; one grouped launch per kernel stage over the "
-                                  "films still running, each film at its own field value"},
-        "sequential": {"value": ev_s / (t_s / 1e3), "unit": UNIT, "ms_per_step": t_s / K,
-                       "evals_per_step": ev_s / K, "speedup_batched": t_s / t_b},
-        "evals_per_step": ev_b / K,
-        "loop_time_s_est": {"batched": len(F) * t_b / K / 1e3, "sequential": len(F) * t_s / K / 1e3},
-        "gpu_launches": int(launches), "clocks": clocks,
+                   "parallelism": "one graph launch per sweep call, an independent branch per film (each with its "
+                                  "own nested device-side minimiser loop)"},
+        "sequential": {"value": ev_s / (t_s / 1e3), "unit": UNIT, "ms_per_step": t_s / K, "evals_per_step": ev_s / K},
+        "batch_kinds": results,
+        "evals_per_step": head["evals_per_step"],
+        "loop_time_s_est": {"batched": len(F) * head["ms_per_step"] / 1e3, "sequential": len(F) * t_s / K / 1e3},
+        "gpu_launches": head["gpu_launches"], "clocks": clocks,
     }
     print(json.dumps(line))
-    batch.close()
     for p in probs:
         p.close()
     return 0
@@ -605,6 +682,10 @@ def main():
                     help="measure only --precision (by default the line also carries the other precision)")
     ap.add_argument("--full-loop", action="store_true",
                     help="time one whole hysteresis loop (every field value, one sweep call) instead of K steps")
+    ap.add_argument("--compare-precisions", action="store_true",
+                    help="one loop in FP32 and one in FP64 on the workload, every FP32 result compared with FP64")
+    ap.add_argument("--values", type=int, default=0,
+                    help="with --compare-precisions: only the first VALUES field values of the sweep")
     ap.add_argument("--max-iter", type=int, default=200000,
                     help="iteration cap per field value (a bounded step for very slow workloads)")
     ap.add_argument("--profile-stages", type=int, default=0,
@@ -633,6 +714,8 @@ def main():
     if args.adjoint:
         return run_adjoint(args, dev)
     w = all_workloads(inputs)[args.workload]()
+    if args.compare_precisions:
+        return run_precision_compare(args, w, dev)
     if args.precision == "mixed":
         if not args.full_loop:
             ap.error("--precision mixed is measured as a whole loop: add --full-loop")

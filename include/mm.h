@@ -332,29 +332,37 @@ MM_API int mm_hysteresis_sweep_mixed(mm_problem *lo, mm_problem *hi, void *m, co
  * Batched sweeps (an extension; the paper sweeps one sample).  A batch
  * references existing problems (of any sizes and precisions; the caller keeps
  * owning them and must not destroy them while the batch exists) and runs
- * their hysteresis sweeps together.
- * Grouped path (every problem film-layout, MM_FP64 or MM_FP32): one sweep
- * call is ONE graph launch.  Its device-side loop runs one minimiser
- * iteration of every problem still running per pass -- one grouped kernel
- * launch per stage and precision over the work items of all those problems --
- * and each problem moves on to its next field value as soon as its
- * minimisation at the current one ends, so problems advance at their own
- * pace.  Each work item runs the problem's own kernel body with the
- * problem's own tile, partial sums and state, so every problem's results
- * equal its own mm_hysteresis_sweep bit for bit.  mm_batch_create gives all
- * members of a precision the tile thread counts of the largest member (one
- * CTA shape per grouped launch): it may change the launch shapes of smaller
- * members, and recaptures their minimiser graphs, so their later single
- * sweeps use the same shapes.
- * Stream path (any bulk-layout or MM_F32X2 member): each problem keeps its own
- * device-side loop and gets a stream of its own; for every field value the
- * batch issues every problem's minimisation on its stream, so the problems
- * run concurrently on the GPU.
- * mm_batch_create returns MM_ERR_ARG for a null or repeated problem (one
- * problem's buffers cannot serve two work lists) and for one whose setup did
- * not finish; the batch owns its tables, graph or streams, released by
- * mm_batch_destroy.  The caller must not destroy a member while the batch
- * exists.
+ * their hysteresis sweeps together.  Three ways to run them (`kind` of
+ * mm_batch_create_kind; mm_batch_create takes MM_BATCH_AUTO):
+ * MM_BATCH_BRANCHES (what MM_BATCH_AUTO selects; any problems): one sweep
+ * call is ONE graph launch.  The graph holds one independent branch per
+ * problem: a device-side loop over the field values whose body sets the
+ * minimiser state, runs the problem's own minimiser loop (its own kernels,
+ * launch shapes and device-side stop rule, nested as a conditional node) and
+ * records the result.  No host work per field value; the GPU interleaves the
+ * branches.  Every problem's results equal its own mm_hysteresis_sweep bit
+ * for bit.
+ * MM_BATCH_GROUPED (every problem film-layout, MM_FP64 or MM_FP32, else
+ * MM_ERR_UNSUPPORTED): one sweep call is ONE graph launch.  Its device-side
+ * loop runs one minimiser iteration of every problem still running per pass
+ * -- one grouped kernel launch per stage and precision over the work items
+ * of all those problems -- and each problem moves on to its next field value
+ * as soon as its minimisation at the current one ends, so problems advance
+ * at their own pace.  Each work item runs the problem's own kernel body with
+ * the problem's own tile, partial sums and state, so every problem's results
+ * equal its own mm_hysteresis_sweep bit for bit.  Creation gives all members
+ * of a precision the tile thread counts of the largest member (one CTA shape
+ * per grouped launch): it may change the launch shapes of smaller members,
+ * and recaptures their minimiser graphs, so their later single sweeps use
+ * the same shapes.
+ * MM_BATCH_STREAMS (any problems): each problem keeps its own minimiser graph
+ * and gets a stream of its own; for every field value the batch issues every
+ * problem's minimisation on its stream from the host.
+ * mm_batch_create(_kind) returns MM_ERR_ARG for a null or repeated problem
+ * (one problem's buffers cannot serve two work lists), for one whose setup
+ * did not finish and for an unknown kind; the batch owns its tables, graph or
+ * streams, released by mm_batch_destroy.  mm_batch_kind returns the kind a
+ * batch runs (MM_BATCH_BRANCHES, _GROUPED or _STREAMS).
  *
  * mm_batch_sweep: as mm_hysteresis_sweep for every problem i with the same
  * field list H_list[n][3] (host, A/m): m_list[i] (host or device, in/out) is
@@ -363,8 +371,11 @@ MM_API int mm_hysteresis_sweep_mixed(mm_problem *lo, mm_problem *hi, void *m, co
  * `stream` is synchronised before returning.  Returns MM_OK if every
  * minimisation converged, else the first non-OK status.
  */
+enum { MM_BATCH_AUTO = 0, MM_BATCH_BRANCHES = 1, MM_BATCH_GROUPED = 2, MM_BATCH_STREAMS = 3 };
 typedef struct mm_batch mm_batch;
 MM_API int mm_batch_create(mm_problem *const *probs, int nprob, mm_batch **out);
+MM_API int mm_batch_create_kind(mm_problem *const *probs, int nprob, int kind, mm_batch **out);
+MM_API int mm_batch_kind(const mm_batch *batch);
 MM_API int mm_batch_destroy(mm_batch *batch);
 MM_API int mm_batch_sweep(mm_batch *batch, void *const *m_list, const double *H_list, int n, int start,
                           const mm_min_opts *opts, double *mavg, mm_min_result *per_step, void *stream);

@@ -168,6 +168,9 @@ int plan(mm_problem *p)
     g.fcex_x = (float)g.cex_x; g.fcex_y = (float)g.cex_y; g.fcex_z = (float)g.cex_z;
     g.fcan = (float)g.can; g.fK = (float)g.K;
     g.fu[0] = (float)g.u[0]; g.fu[1] = (float)g.u[1]; g.fu[2] = (float)g.u[2];
+    g.wcex[0] = dfloat(g.cex_x); g.wcex[1] = dfloat(g.cex_y); g.wcex[2] = dfloat(g.cex_z);
+    g.wcan = dfloat(g.can); g.wK = dfloat(g.K);
+    for (int c = 0; c < 3; ++c) g.wu[c] = dfloat(g.u[c]);
     g.fd_nx.init(gr.nx); g.fd_ny.init(gr.ny);
     g.fd_padx.init(g.Px - gr.nx > 0 ? g.Px - gr.nx : 1);
     g.fd_pady.init(g.Py - gr.ny > 0 ? g.Py - gr.ny : 1);
@@ -272,6 +275,7 @@ int build_graph(mm_problem *p)
         if (lr != MM_OK || ee) { rc = MM_ERR_CUDA; break; }
         if (cudaGraphInstantiate(&p->gexec, p->graph, 0)) { rc = MM_ERR_CUDA; break; }
         p->graph_ready = 1;
+        ++p->graph_gen;
     } while (0);
     if (rc != MM_OK) {
         cudaError_t e = cudaGetLastError();

@@ -17,9 +17,17 @@
 // result equals its own single sweep bit for bit.  A problem that has
 // converged skips its work items until the field value ends.
 //
-// Bulk-layout problems (three-dimensional grids) keep the stream path: each
-// problem's own minimiser graph on a stream of its own, all streams issued
-// per field value so the problems overlap on the GPU.
+// Branch graph (the default; any problems): one sweep call is ONE graph
+// launch whose graph holds one independent branch per problem: a
+// conditional WHILE node over the problem's field values whose body sets the
+// minimiser state for the next value, runs the problem's own minimiser loop
+// (a nested conditional WHILE node around its three kernels, the same body
+// as its own minimiser graph) and records the result.  The branches share
+// nothing, so the GPU interleaves the problems' kernels as it would
+// independent streams, with no host launch per field value.
+//
+// Stream path: each problem's own minimiser graph on a stream of its own,
+// all streams issued per field value so the problems overlap on the GPU.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -195,10 +203,11 @@ __device__ void init_one(GInit *init, int i, int j, const double *H, const GCtl 
     st->tau0 = init[i].tau0; st->tol_abs = init[i].tol_abs;
     st->Hext[0] = h0; st->Hext[1] = h1; st->Hext[2] = h2;
     st->Hextf[0] = (float)h0; st->Hextf[1] = (float)h1; st->Hextf[2] = (float)h2;
+    st->Hextw[0] = dfloat(h0); st->Hextw[1] = dfloat(h1); st->Hextw[2] = dfloat(h2);
     st->max_iter = c.max_iter; st->step_kind = c.step_kind;
     st->tau_rule = c.tau_rule; st->kappa = c.kappa;
     st->timeout_ns = c.timeout_ns; st->t_start_ns = 0;
-    st->k = 0; st->tau = init[i].tau0; st->tauf = (float)init[i].tau0; st->status = MMS_RUNNING; st->evals = 0;
+    st->k = 0; st->tau = init[i].tau0; st->tauf = (float)init[i].tau0; st->tauw = dfloat(init[i].tau0); st->status = MMS_RUNNING; st->evals = 0;
     st->launches = 1;
     st->max_torque = 0;
     init[i].j = j;
@@ -244,6 +253,30 @@ __global__ void k_group_advance(GInit *init, int n, const double *H, const GCtl 
     cudaGraphSetConditional(h, active > 0 ? 1u : 0u);
 }
 
+// Branch graph: problem i's next field value (its index init[i].j), and the
+// nested minimiser loop's condition set to run
+__global__ void k_branch_init(GInit *init, int i, const double *H, const GCtl *ctl, cudaGraphConditionalHandle inner)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    init_one(init, i, init[i].j, H, *ctl);
+    cudaGraphSetConditional(inner, 1u);
+}
+
+// Branch graph: record problem i's field value and go on while values remain
+__global__ void k_branch_record(GInit *init, int i, const GCtl *ctl, cudaGraphConditionalHandle outer)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const MinState *st = init[i].st;
+    const int j = init[i].j;
+    StepRecord r;
+    r.mavg[0] = st->mavg[0]; r.mavg[1] = st->mavg[1]; r.mavg[2] = st->mavg[2];
+    r.max_torque = st->max_torque; r.energy = st->energy[4];
+    r.iters = st->k; r.evals = st->evals; r.launches = st->launches + 1; r.status = st->status;
+    init[i].rec[j] = r;
+    init[i].j = j + 1;
+    cudaGraphSetConditional(outer, j + 1 < ctl->n ? 1u : 0u);
+}
+
 // device tables of one precision group
 template <typename T>
 struct Group {
@@ -263,12 +296,13 @@ struct Group {
 
 struct mm_batch {
     std::vector<mm_problem *> probs;
+    int kind = MM_BATCH_BRANCHES;
+    std::vector<int> gens;       // branch graph: the members' graph generations it was built from
     // stream path (bulk-layout problems present)
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> done;
     cudaEvent_t start_ev = nullptr;
     // grouped path
-    bool grouped = false;
     // groups by precision and size class: large problems (>= 65536 cells)
     // and small ones; each group's stages run as a branch of its own in the
     // loop body, so the groups' kernels overlap on the GPU
@@ -497,6 +531,71 @@ int build_batch_graph(mm_batch *b)
     return MM_OK;
 }
 
+// Branch graph: per problem a WHILE over its field values { init; WHILE
+// { its three minimiser kernels }; record }, the branches independent.
+int build_branch_graph(mm_batch *b)
+{
+    const int n = (int)b->probs.size();
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e) { mm_set_cuda_error(e, "cudaStreamCreate"); return MM_ERR_CUDA; }
+    int rc = MM_OK;
+    auto while_node = [](cudaGraph_t g, cudaGraphConditionalHandle h, const cudaGraphNode_t *dep, size_t ndep,
+                         cudaGraphNode_t *node, cudaGraph_t *body) -> cudaError_t {
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaError_t err = cudaGraphAddNode(node, g, dep, nullptr, ndep, &np);
+        if (!err) *body = np.conditional.phGraph_out[0];
+        return err;
+    };
+    do {
+        if ((e = cudaGraphCreate(&b->graph, 0))) break;
+        for (int i = 0; i < n && !e && rc == MM_OK; ++i) {
+            mm_problem *p = b->probs[i];
+            // outer loop over field values: runs at least once per launch (default 1)
+            cudaGraphConditionalHandle ho, hi;
+            cudaGraphNode_t outer, init_node, inner;
+            cudaGraph_t obody, ibody;
+            if ((e = cudaGraphConditionalHandleCreate(&ho, b->graph, 1, cudaGraphCondAssignDefault))) break;
+            if ((e = while_node(b->graph, ho, nullptr, 0, &outer, &obody))) break;
+            if ((e = cudaGraphConditionalHandleCreate(&hi, obody, 0, 0))) break;
+            if ((e = cudaStreamBeginCaptureToGraph(cs, obody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed))) break;
+            k_branch_init<<<1, 32, 0, cs>>>(b->init_dev, i, b->H_dev, b->ctl_dev, hi);
+            cudaGraph_t out = obody;
+            if ((e = cudaStreamEndCapture(cs, &out))) break;
+            size_t nn = 1;
+            if ((e = cudaGraphGetNodes(obody, &init_node, &nn)) || nn != 1) { if (!e) e = cudaErrorUnknown; break; }
+            if ((e = while_node(obody, hi, &init_node, 1, &inner, &ibody))) break;
+            if ((e = cudaStreamBeginCaptureToGraph(cs, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed))) break;
+            const int lr = mm_launch_min_body(p, hi, cs, 1);
+            out = ibody;
+            e = cudaStreamEndCapture(cs, &out);
+            if (lr != MM_OK) { rc = lr; break; }
+            if (e) break;
+            if ((e = cudaStreamBeginCaptureToGraph(cs, obody, &inner, nullptr, 1, cudaStreamCaptureModeRelaxed))) break;
+            k_branch_record<<<1, 32, 0, cs>>>(b->init_dev, i, b->ctl_dev, ho);
+            out = obody;
+            const cudaError_t le = cudaGetLastError();
+            e = cudaStreamEndCapture(cs, &out);
+            if (le) e = le;
+        }
+        if (e || rc != MM_OK) break;
+        if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0))) break;
+    } while (0);
+    cudaStreamDestroy(cs);
+    if (e || rc != MM_OK) {
+        if (e) mm_set_cuda_error(e, "batch branch graph");
+        if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+        return rc != MM_OK ? rc : MM_ERR_CUDA;
+    }
+    b->gens.clear();
+    for (auto *p : b->probs) b->gens.push_back(p->graph_gen);
+    return MM_OK;
+}
+
 // One CTA shape per grouped launch: every member of a precision group takes
 // the tile whose thread count is the largest not above that of the group's
 // largest problem (which carries most of the work and keeps its own tuned
@@ -572,6 +671,18 @@ int create_grouped(mm_batch *b)
     }
     b->H_cap = 1;
     return MM_OK;
+}
+
+int create_branches(mm_batch *b)
+{
+    cudaError_t e;
+    if ((e = cudaMalloc((void **)&b->init_dev, sizeof(GInit) * b->probs.size())) ||
+        (e = cudaMalloc((void **)&b->ctl_dev, sizeof(GCtl))) || (e = cudaMalloc((void **)&b->H_dev, sizeof(double) * 3))) {
+        mm_set_cuda_error(e, "cudaMalloc(batch)");
+        return MM_ERR_OOM;
+    }
+    b->H_cap = 1;
+    return build_branch_graph(b);
 }
 
 int create_streams(mm_batch *b)
@@ -655,11 +766,20 @@ int sweep_streams(mm_batch *b, void *const *m_list, const double *H_list, int n,
     return rc;
 }
 
-int sweep_grouped(mm_batch *b, void *const *m_list, const double *H_list, int n, int start, const mm_min_opts *opts,
-                  cudaStream_t s)
+// grouped path and branch graph: one graph launch per sweep call
+int sweep_graph(mm_batch *b, void *const *m_list, const double *H_list, int n, int start, const mm_min_opts *opts,
+                cudaStream_t s)
 {
     const size_t P = b->probs.size();
     cudaError_t e;
+    bool stale = false;   // the branch graph holds the members' kernel parameters: recapture after a member's
+    if (b->kind == MM_BATCH_BRANCHES)   // own graph was recaptured (e.g. a new per-cell anisotropy buffer)
+        for (size_t i = 0; i < P; ++i) stale = stale || b->gens[i] != b->probs[i]->graph_gen;
+    if (stale) {
+        cudaStreamSynchronize(s);
+        if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+        if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    }
     if (b->H_cap < n) {
         // the graph bakes in the field buffer's address: recapture it with the new one
         double *nh = nullptr;
@@ -672,7 +792,7 @@ int sweep_grouped(mm_batch *b, void *const *m_list, const double *H_list, int n,
         if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
     }
     if (!b->exec) {
-        int rc = build_batch_graph(b);
+        int rc = b->kind == MM_BATCH_BRANCHES ? build_branch_graph(b) : build_batch_graph(b);
         if (rc) return rc;
     }
     // per-sweep tables: states, records, tau0 and the stop threshold of every problem
@@ -694,7 +814,7 @@ int sweep_grouped(mm_batch *b, void *const *m_list, const double *H_list, int n,
     ctl.timeout_ns = opts->timeout_s > 0 ? (unsigned long long)(opts->timeout_s * 1e9) : 0ull;
     ctl.kappa = opts->tau_kappa > 0 ? opts->tau_kappa : 0.5;
     e = cudaSuccess;
-    for (auto &G : b->g64) if (!e) e = refresh_group(b, G, s);
+    for (auto &G : b->g64) if (!e) e = refresh_group(b, G, s);   // (no groups in a branch graph)
     for (auto &G : b->g32) if (!e) e = refresh_group(b, G, s);
     if (e ||
         (e = cudaMemcpyAsync(b->init_dev, init.data(), sizeof(GInit) * P, cudaMemcpyHostToDevice, s)) ||
@@ -721,24 +841,36 @@ int sweep_grouped(mm_batch *b, void *const *m_list, const double *H_list, int n,
 
 } // namespace
 
-extern "C" MM_API int mm_batch_create(mm_problem *const *probs, int n, mm_batch **out)
+extern "C" MM_API int mm_batch_create_kind(mm_problem *const *probs, int n, int kind, mm_batch **out)
 {
-    if (!probs || n < 1 || !out) return MM_ERR_ARG;
+    if (!probs || n < 1 || !out || kind < MM_BATCH_AUTO || kind > MM_BATCH_STREAMS) return MM_ERR_ARG;
     // a problem listed twice would have its buffers used by two work lists at once
     std::vector<mm_problem *> sorted(probs, probs + n);
     std::sort(sorted.begin(), sorted.end());
     if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return MM_ERR_ARG;
     for (int i = 0; i < n; ++i)
         if (!probs[i] || !probs[i]->graph_ready) return MM_ERR_ARG;
+    // grouped launches serve film-layout problems in double or float
+    bool all_film = true;
+    for (int i = 0; i < n; ++i) all_film = all_film && !probs[i]->g.bulk && probs[i]->precision != MM_F32X2;
+    if (kind == MM_BATCH_GROUPED && !all_film) return MM_ERR_UNSUPPORTED;
     mm_batch *b = new (std::nothrow) mm_batch;
     if (!b) return MM_ERR_OOM;
     b->probs.assign(probs, probs + n);
-    bool all_film = true;
-    // grouped launches serve film-layout problems in double or float; bulk
-    // grids and double-float problems take the stream path
-    for (int i = 0; i < n; ++i) all_film = all_film && !probs[i]->g.bulk && probs[i]->precision != MM_F32X2;
-    b->grouped = all_film;
-    const int rc = b->grouped ? create_grouped(b) : create_streams(b);
+    b->kind = kind == MM_BATCH_AUTO ? MM_BATCH_BRANCHES : kind;
+    int rc = b->kind == MM_BATCH_BRANCHES ? create_branches(b)
+           : b->kind == MM_BATCH_GROUPED  ? create_grouped(b)
+                                          : create_streams(b);
+    if (rc == MM_ERR_CUDA && kind == MM_BATCH_AUTO) {
+        // a runtime that cannot build the nested graph: the grouped launches
+        // (film-layout problems) or the streams instead
+        free_batch(b);
+        cudaGetLastError();
+        if (!(b = new (std::nothrow) mm_batch)) return MM_ERR_OOM;
+        b->probs.assign(probs, probs + n);
+        b->kind = all_film ? MM_BATCH_GROUPED : MM_BATCH_STREAMS;
+        rc = all_film ? create_grouped(b) : create_streams(b);
+    }
     if (rc) {
         if (rc == MM_ERR_CUDA && !mm_last_cuda_error()[0]) mm_set_cuda_error(cudaGetLastError(), "mm_batch_create");
         free_batch(b);
@@ -747,6 +879,13 @@ extern "C" MM_API int mm_batch_create(mm_problem *const *probs, int n, mm_batch 
     *out = b;
     return MM_OK;
 }
+
+extern "C" MM_API int mm_batch_create(mm_problem *const *probs, int n, mm_batch **out)
+{
+    return mm_batch_create_kind(probs, n, MM_BATCH_AUTO, out);
+}
+
+extern "C" MM_API int mm_batch_kind(const mm_batch *b) { return b ? b->kind : MM_ERR_ARG; }
 
 extern "C" MM_API int mm_batch_destroy(mm_batch *b)
 {
@@ -770,10 +909,10 @@ extern "C" MM_API int mm_batch_sweep(mm_batch *b, void *const *m_list, const dou
     int rc;
     for (size_t i = 0; i < P; ++i)
         if ((rc = ensure_records(b->probs[i], n))) return rc;
-    if (b->grouped) {
+    if (b->kind != MM_BATCH_STREAMS) {
         // the records' addresses are written per sweep into the init table,
         // after ensure_records may have moved them
-        rc = sweep_grouped(b, m_list, H_list, n, start, opts, s);
+        rc = sweep_graph(b, m_list, H_list, n, start, opts, s);
     } else {
         rc = sweep_streams(b, m_list, H_list, n, start, opts, s);
     }
@@ -781,8 +920,7 @@ extern "C" MM_API int mm_batch_sweep(mm_batch *b, void *const *m_list, const dou
         cudaStreamSynchronize(s);
         return rc;
     }
-    // grouped: per field value 1 graph launch (init, record) plus 3 grouped
-    // kernels per precision and a condition kernel per iteration -- shared by
-    // all problems, so per problem the record keeps its own count
+    // per problem the record keeps its own count (grouped: the grouped
+    // kernels and the condition kernel are shared by all problems)
     return collect(b, n, start, mavg, per_step, s, -1);
 }

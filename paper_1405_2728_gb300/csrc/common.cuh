@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <type_traits>
 #include <stdint.h>
 
 #include "../../include/mm.h"
@@ -70,8 +71,10 @@ struct MinState {
     double energy[5];         // demag, exchange, anisotropy, zeeman, total (J) at iterate k
     double mavg[3];
     long launches;            // kernels launched by the loop body so far
-    float Hextf[3];           // Hext and tau rounded once for the float kernels
+    float Hextf[3];           // Hext and tau rounded once for the float kernels,
     float tauf;
+    dfloat Hextw[3];          // and converted once to double-word pairs for the double-word
+    dfloat tauw;              // kernels (a conversion per thread would run on the FP64 pipe)
     double bb[3];             // sums s.s, s.y, y.y over cells at iterate k (0 at k = 0)
     int tau_rule;             // MM_TAU_ALTERNATE or MM_TAU_ADAPTIVE
     double kappa;             // threshold of the adaptive rule
@@ -145,6 +148,7 @@ struct Geom {
     // the same constants rounded once to float for the float kernels (a
     // conversion per thread would run on the slow FP64 pipe)
     float fcex_x, fcex_y, fcex_z, fcan, fK, fu[3];
+    dfloat wcex[3], wcan, wK, wu[3];   // and as double-word pairs for the double-word kernels
     int lty;                       // log2(TY)
     FastDiv fd_nx, fd_ny, fd_padx, fd_pady;  // divisors nx, ny, Px - nx, Py - ny
     int stage;                     // k_xinv (float) stages its stencil rows with 16-byte cp.async
@@ -185,6 +189,12 @@ template <typename T> __host__ __device__ __forceinline__ T pick(double d, float
 {
     if constexpr (sizeof(T) == 4) return f;
     else return d;
+}
+// the same with the double-word copy for the double-word kernels
+template <typename T> __host__ __device__ __forceinline__ T pick(double d, float f, dfloat w)
+{
+    if constexpr (std::is_same<T, dfloat>::value) return w;
+    else return pick<T>(d, f);
 }
 
 
@@ -261,6 +271,7 @@ struct mm_problem {
     cudaGraphExec_t gexec;
     cudaGraphConditionalHandle cond;
     int graph_ready;
+    int graph_gen;         // incremented at every capture of the minimiser graph
     int dev;
     // device-side conjugate-gradient loop of the adjoint (built on first use)
     cudaGraph_t adj_graph;

@@ -119,7 +119,7 @@ __device__ __forceinline__ void xfwd_body(const Geom &g, const FieldPtrs<T, F> &
             src = cur ? P.mbuf[0] : P.mbuf[1];
             dst = cur ? P.mbuf[1] : P.mbuf[0];
             gp = ((k - 1) & 1) ? P.gbuf[1] : P.gbuf[0];
-            tau = pick<T>(st->tau, st->tauf);
+            tau = pick<T>(st->tau, st->tauf, st->tauw);
             step_kind = st->step_kind;
         } else {
             src = cur ? P.mbuf[1] : P.mbuf[0];
@@ -505,6 +505,7 @@ __device__ void finish_iteration(const Geom &g, double *partials, int nblk, MinS
         }
         st->tau = tau;
         st->tauf = (float)tau;
+        st->tauw = dfloat(tau);
         st->k = k + 1;
         stop = 0;
     }
@@ -632,17 +633,18 @@ __device__ __forceinline__ void xinv_body(const Geom &g, const FieldPtrs<T, F> &
     // local terms
     T he0, he1, he2;
     if (MODE == MODE_MIN) {
-        he0 = pick<T>(st->Hext[0], st->Hextf[0]);
-        he1 = pick<T>(st->Hext[1], st->Hextf[1]);
-        he2 = pick<T>(st->Hext[2], st->Hextf[2]);
+        he0 = pick<T>(st->Hext[0], st->Hextf[0], st->Hextw[0]);
+        he1 = pick<T>(st->Hext[1], st->Hextf[1], st->Hextw[1]);
+        he2 = pick<T>(st->Hext[2], st->Hextf[2], st->Hextw[2]);
     } else {
         he0 = (T)hx0; he1 = (T)hx1; he2 = (T)hx2;
     }
-    const T cx = pick<T>(g.cex_x, g.fcex_x), cy = pick<T>(g.cex_y, g.fcex_y), cz = pick<T>(g.cex_z, g.fcex_z);
-    const T can = pick<T>(g.can, g.fcan);
+    const T cx = pick<T>(g.cex_x, g.fcex_x, g.wcex[0]), cy = pick<T>(g.cex_y, g.fcex_y, g.wcex[1]),
+            cz = pick<T>(g.cex_z, g.fcex_z, g.wcex[2]);
+    const T can = pick<T>(g.can, g.fcan, g.wcan);
     const T kfac = (T)0.5 * can;  // 1/(mu0 Ms)
-    const T Kuni = pick<T>(g.K, g.fK), ux = pick<T>(g.u[0], g.fu[0]), uy = pick<T>(g.u[1], g.fu[1]),
-            uz = pick<T>(g.u[2], g.fu[2]);
+    const T Kuni = pick<T>(g.K, g.fK, g.wK), ux = pick<T>(g.u[0], g.fu[0], g.wu[0]),
+            uy = pick<T>(g.u[1], g.fu[1], g.wu[1]), uz = pick<T>(g.u[2], g.fu[2], g.wu[2]);
     const T hs = (T)P.hscale;
     Acc<T> red[NSL];
 #pragma unroll

@@ -148,6 +148,7 @@ template <typename T, typename F> cudaError_t autotune_t(mm_problem *p, const in
     ms.k = 1;
     ms.tau = ms.tau0 = 1e-9;
     ms.tauf = 1e-9f;
+    ms.tauw = dfloat(1e-9);
     ms.max_iter = 1L << 40;
     ms.status = MMS_RUNNING;
     if ((e = cudaMemcpyAsync(p->st, &ms, sizeof ms, cudaMemcpyHostToDevice, s)) || (e = cudaStreamSynchronize(s)))

@@ -54,10 +54,11 @@ __global__ void k_init_state(MinState *st, double tau0, double tol_abs, double h
     st->tau0 = tau0; st->tol_abs = tol_abs;
     st->Hext[0] = h0; st->Hext[1] = h1; st->Hext[2] = h2;
     st->Hextf[0] = (float)h0; st->Hextf[1] = (float)h1; st->Hextf[2] = (float)h2;
+    st->Hextw[0] = dfloat(h0); st->Hextw[1] = dfloat(h1); st->Hextw[2] = dfloat(h2);
     st->max_iter = max_iter; st->step_kind = step_kind;
     st->tau_rule = tau_rule; st->kappa = kappa;
     st->timeout_ns = timeout_ns; st->t_start_ns = 0;
-    st->k = 0; st->tau = tau0; st->tauf = (float)tau0; st->status = MMS_RUNNING; st->evals = 0; st->launches = 1;
+    st->k = 0; st->tau = tau0; st->tauf = (float)tau0; st->tauw = dfloat(tau0); st->status = MMS_RUNNING; st->evals = 0; st->launches = 1;
     st->max_torque = 0;
 }
 

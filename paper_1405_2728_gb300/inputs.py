@@ -221,4 +221,7 @@ BULK_WORKLOADS = {
     # the same 512^3 padded grid with fewer cells (~2 GB on the device): the
     # case the bulk kernels are profiled on
     "cube_160": lambda: granular_cube(160, 64, edge=320e-9),
+    # the same recipe (2 nm cells, 64 grains, 481-value ramp) on 64^3 cells:
+    # small enough for whole FP32 and FP64 loops to be compared
+    "cube_64": lambda: granular_cube(64, 64, edge=128e-9),
 }

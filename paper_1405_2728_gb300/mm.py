@@ -24,6 +24,7 @@ MM_ERR_NOT_CONVERGED, MM_ERR_NONFINITE, MM_ERR_TIMEOUT, MM_ERR_UNSUPPORTED = -4,
 MM_FP64, MM_FP32, MM_F32X2 = 0, 1, 2
 MM_STEP_CAYLEY, MM_STEP_NORMALIZE = 0, 1
 MM_TAU_ALTERNATE, MM_TAU_ADAPTIVE = 0, 1
+MM_BATCH_AUTO, MM_BATCH_BRANCHES, MM_BATCH_GROUPED, MM_BATCH_STREAMS = 0, 1, 2, 3
 
 
 class mm_grid(ctypes.Structure):
@@ -108,6 +109,8 @@ def lib():
         L.mm_min_inspect.argtypes = [c_void_p, POINTER(mm_min_state), c_void_p, c_void_p, c_void_p, c_void_p,
                                      c_void_p]
         L.mm_batch_create.argtypes = [POINTER(c_void_p), c_int, POINTER(c_void_p)]
+        L.mm_batch_create_kind.argtypes = [POINTER(c_void_p), c_int, c_int, POINTER(c_void_p)]
+        L.mm_batch_kind.argtypes = [c_void_p]
         L.mm_batch_destroy.argtypes = [c_void_p]
         L.mm_batch_sweep.argtypes = [c_void_p, POINTER(c_void_p), dp, c_int, c_int, POINTER(mm_min_opts), dp,
                                      POINTER(mm_min_result), c_void_p]
@@ -117,7 +120,7 @@ def lib():
         for name in ("mm_newell", "mm_newell_static", "mm_setup_geometry", "mm_destroy", "mm_heff", "mm_energy", "mm_minimize",
                      "mm_hysteresis_sweep", "mm_problem_info", "mm_kernel_times", "mm_energy_gradient",
                      "mm_hessian_vec", "mm_adjoint_dK", "mm_set_anisotropy", "mm_hysteresis_sweep_mixed", "mm_batch_create",
-                     "mm_batch_destroy", "mm_batch_sweep", "mm_probe_fma", "mm_min_inspect"):
+                     "mm_batch_create_kind", "mm_batch_kind", "mm_batch_destroy", "mm_batch_sweep", "mm_probe_fma", "mm_min_inspect"):
             getattr(L, name).restype = c_int
         _lib = L
     return _lib
@@ -423,11 +426,18 @@ class Batch:
             pass
 
 
-def mm_batch_create(probs) -> Batch:
+def mm_batch_create(probs, kind=None) -> Batch:
+    """A batch over probs; kind one of MM_BATCH_AUTO (default: the branch
+    graph), MM_BATCH_BRANCHES, MM_BATCH_GROUPED, MM_BATCH_STREAMS."""
     arr = (c_void_p * len(probs))(*[p.handle for p in probs])
     h = c_void_p()
-    _check(lib().mm_batch_create(arr, len(probs), ctypes.byref(h)), "mm_batch_create")
+    _check(lib().mm_batch_create_kind(arr, len(probs), MM_BATCH_AUTO if kind is None else int(kind), ctypes.byref(h)),
+           "mm_batch_create_kind")
     return Batch(h, probs)
+
+
+def mm_batch_kind(batch: Batch) -> int:
+    return lib().mm_batch_kind(batch.handle)
 
 
 def mm_batch_destroy(batch: Batch):
