@@ -339,7 +339,8 @@ def run_full_loop(args, w, prob, m, F, opts, stream, tdt, esz, info, dev):
             "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE_LABEL[args.precision], "data": "synthetic",
             "config": {"workload": w.name, "cells": [w.nx, w.ny, w.nz], "precision": args.precision,
-                       "step": f"one whole loop: {len(F)} field values minimised to tol {w.tol:g}"},
+                       "step": f"one whole loop: {len(F)} field values minimised to tol {w.tol:g}",
+                       "tau_rule": args.tau_rule},
             "loop_time_s": sec, "loop_evals": int(evals),
             "converged_field_values": int(sum(r.converged for r in res)), "field_values": len(F),
             "status": int(st), "gpu_launches": int(sum(r.kernel_launches for r in res)),
@@ -680,6 +681,8 @@ def main():
                     help="time the implicit adjoint (differentiation extension) on the 128x64x2 film instead")
     ap.add_argument("--only", action="store_true",
                     help="measure only --precision (by default the line also carries the other precision)")
+    ap.add_argument("--tau-rule", default="alternate", choices=["alternate", "adaptive"],
+                    help="step-size rule of the minimiser (Section 2 alternation, or the adaptive switch)")
     ap.add_argument("--full-loop", action="store_true",
                     help="time one whole hysteresis loop (every field value, one sweep call) instead of K steps")
     ap.add_argument("--compare-precisions", action="store_true",
@@ -729,7 +732,8 @@ def main():
     F = w.fields()
     hdir = F[int(np.argmax(np.linalg.norm(F, axis=1)))]
     hdir = hdir / np.linalg.norm(hdir)
-    opts = mm.make_opts(tol=w.tol, max_iter=args.max_iter)
+    opts = mm.make_opts(tol=w.tol, max_iter=args.max_iter,
+                        tau_rule=mm.MM_TAU_ADAPTIVE if args.tau_rule == "adaptive" else mm.MM_TAU_ALTERNATE)
     stream = torch.cuda.current_stream(dev)
     m = torch.from_numpy(w.initial_m()).to(device=dev, dtype=tdt).contiguous()
     flush = torch.empty(int(256 * 2**20) // 4, dtype=torch.float32, device=dev)  # > 2x L2

@@ -22,7 +22,8 @@ plane off the long edge (toward +y) and off the short edge (toward +x).  The
 sweep is +50 -> -50 -> +50 mT.  The start is saturated along the field, with
 the seeded 1e-3 tilt.
 
-    python -m paper_1405_2728_gb300.study [--precision fp64|fp32] [--cells 10,5] [--steps 1,0.5]
+    python -m paper_1405_2728_gb300.study [--precision fp64|fp32|f32x2] [--cells 10,5] [--steps 1,0.5]
+                                          [--tau-rule alternate|adaptive]
 """
 from __future__ import annotations
 
@@ -74,7 +75,8 @@ def loop_metrics(H: np.ndarray, mavg: np.ndarray, hhat: np.ndarray) -> dict:
     return out
 
 
-def run_loop(cell_nm: float, step_mT: float, edge: str, precision: int, tol: float = 1e-5, seed: int = 1405):
+def run_loop(cell_nm: float, step_mT: float, edge: str, precision: int, tol: float = 1e-5, seed: int = 1405,
+             tau_rule: int = mm.MM_TAU_ALTERNATE):
     """One SP1 loop.  Returns (metrics, remanent m (3, nz, ny, nx) as numpy, evals, seconds)."""
     import torch
 
@@ -84,10 +86,10 @@ def run_loop(cell_nm: float, step_mT: float, edge: str, precision: int, tol: flo
     prob = mm.mm_setup_geometry(grid, mm.make_material(8.0e5, 1.3e-11, 500.0), precision)
     hhat = direction(edge)
     H = sweep_fields(hhat, 50.0, step_mT)
-    dt = torch.float64 if precision == mm.MM_FP64 else torch.float32
+    dt = torch.float32 if precision == mm.MM_FP32 else torch.float64
     m0 = inputs.tilted_uniform_m((nz, ny, nx), seed, axis=tuple(hhat))
     m = torch.from_numpy(m0).to(device="cuda", dtype=dt).contiguous()
-    opts = mm.make_opts(tol=tol, max_iter=200000)
+    opts = mm.make_opts(tol=tol, max_iter=200000, tau_rule=tau_rule)
     i0 = int(np.argmin(np.abs(H @ hhat)[: len(H) // 2 + 1]))  # zero field on the descending branch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -107,13 +109,14 @@ def run_loop(cell_nm: float, step_mT: float, edge: str, precision: int, tol: flo
     return met, rem, evals, dt_s
 
 
-def convergence_study(precision: int = mm.MM_FP64, cells_nm=(10.0, 5.0), steps_mT=(1.0, 0.5)):
+def convergence_study(precision: int = mm.MM_FP64, cells_nm=(10.0, 5.0), steps_mT=(1.0, 0.5),
+                      tau_rule: int = mm.MM_TAU_ALTERNATE):
     rows = []
     remanence = {}
     for c in cells_nm:
         for s in steps_mT:
             for edge in ("long", "short"):
-                met, rem, ev, sec = run_loop(c, s, edge, precision)
+                met, rem, ev, sec = run_loop(c, s, edge, precision, tau_rule=tau_rule)
                 rows.append({"cell_nm": c, "step_mT": s, "field_edge": edge, **met,
                              "evals": int(ev), "seconds": sec})
                 remanence[(c, s, edge)] = rem
@@ -130,19 +133,22 @@ def convergence_study(precision: int = mm.MM_FP64, cells_nm=(10.0, 5.0), steps_m
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "f32x2"])
+    ap.add_argument("--tau-rule", default="alternate", choices=["alternate", "adaptive"],
+                    help="step-size rule: alternate tau^1/tau^2 (Section 2) or the adaptive switch")
     ap.add_argument("--cells", default="10,5", help="cell sizes in nm, comma separated")
     ap.add_argument("--steps", default="1,0.5", help="field steps in mT, comma separated")
     args = ap.parse_args(argv)
-    prec = mm.MM_FP64 if args.precision == "fp64" else mm.MM_FP32
+    prec = {"fp64": mm.MM_FP64, "fp32": mm.MM_FP32, "f32x2": mm.MM_F32X2}[args.precision]
+    rule = mm.MM_TAU_ADAPTIVE if args.tau_rule == "adaptive" else mm.MM_TAU_ALTERNATE
     rows, rem = convergence_study(prec, [float(x) for x in args.cells.split(",")],
-                                  [float(x) for x in args.steps.split(",")])
+                                  [float(x) for x in args.steps.split(",")], rule)
     mu0 = inputs.MU0
     for r in rows:  # fields in mT for reading
         for k in ("H_sw", "H_c"):
             if r[k] is not None:
                 r[k + "_mT"] = r[k] * mu0 * 1e3
-    print(json.dumps({"study": "sp1_convergence", "precision": args.precision, "loops": rows,
+    print(json.dumps({"study": "sp1_convergence", "precision": args.precision, "tau_rule": args.tau_rule, "loops": rows,
                       "remanence_long_vs_short": rem}))
 
 
