@@ -392,7 +392,7 @@ extern "C" int mm_setup_geometry(const mm_grid *grid, const mm_material *mat, in
     p->mat.K_cell = nullptr;
     p->mat.u_cell = nullptr;
     p->precision = precision;
-    p->esz = precision == MM_FP32 ? 4 : 8;   // MM_F32X2: double fields, tensor as float pairs (8 bytes)
+    p->esz = precision == MM_FP32 ? 4 : 8;   // MM_F32X2: fields and tensor as float pairs (8 bytes), like double
     int rc = plan(p);
     if (rc != MM_OK) { delete p; return rc; }
     cudaGetDevice(&p->dev);

@@ -1,6 +1,7 @@
-"""Double-float precision (MM_F32X2, an extension): fields in double, the
-FFTs and the demagnetisation convolution in pairs of floats (about 48
-significant bits), the local terms, the step and the reductions in double.
+"""Double-float precision (MM_F32X2, an extension): the caller's arrays in
+double; the iterates, the FFTs, the demagnetisation convolution, the local
+terms, the step and the per-CTA sums in pairs of floats (about 48
+significant bits); the sums across CTAs and the step size in double.
 
 Bars.  H_eff against the FP64 oracle: rel-L2 <= 1e-10, the FP64 target (the
 double-float FFT carries ~1e-14 per element times its log depth).  Energy
