@@ -38,6 +38,9 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # nominal FMA lanes per SM per clock (the measured rates come from mm_probe_fma)
 FP64_FMA_PER_SM_CLK = 2
 FP32_FMA_PER_SM_CLK = 128
+# the timed steps' field values are far from switching; a whole loop needs more evaluations there
+LOOP_NOTE = ("field values x the mean time of the timed steps; the whole loop, timed by --full-loop, takes longer: "
+             "near the switching field a value needs thousands of evaluations")
 DW_ADD_INSTRUCTIONS = 11      # FP32 instructions of one double-word (float pair) addition
 PRECISIONS = {"fp64": 0, "fp32": 1, "f32x2": 2}   # mm.MM_FP64, mm.MM_FP32, mm.MM_F32X2
 DTYPE_LABEL = {"fp64": "f64", "fp32": "f32", "f32x2": "f32x2 (double-word) fields, FFT, convolution and local terms"}
@@ -571,7 +574,8 @@ def run_batch(args, ws, rank, local, dev):
         "sequential": {"value": ev_s / (t_s / 1e3), "unit": UNIT, "ms_per_step": t_s / K, "evals_per_step": ev_s / K},
         "batch_kinds": results,
         "evals_per_step": head["evals_per_step"],
-        "loop_time_s_est": {"batched": len(F) * head["ms_per_step"] / 1e3, "sequential": len(F) * t_s / K / 1e3},
+        "loop_time_s_extrapolated": {"batched": len(F) * head["ms_per_step"] / 1e3, "sequential": len(F) * t_s / K / 1e3},
+        "loop_time_note": LOOP_NOTE,
         "gpu_launches": head["gpu_launches"], "clocks": clocks,
     }
     print(json.dumps(line))
@@ -871,7 +875,8 @@ def main():
                    "fields_mT": [round(float(F[(args.warmup + j) % len(F)] @ hdir) * inputs.MU0 * 1e3, 3) for j in range(K)],
                    "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas{ws}"},
         "evals_per_step": evals / K, "wall_s": t_wall,
-        "loop_time_s_est": (len(F) * evals / K) / value,
+        "loop_time_s_extrapolated": (len(F) * evals / K) / value,
+        "loop_time_note": LOOP_NOTE,
         "statuses": statuses,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(3 * w.ncells * esz + 24),
                 "d2h_bytes_per_step": int(3 * w.ncells * esz + 64)},
@@ -897,7 +902,7 @@ def main():
         qinfo = mm.mm_problem_info(qp)
         line[q] = {"value": qev / (qms / 1e3), "unit": UNIT, "dtype": DTYPE_LABEL[q],
                    "ms_per_step": qms / K, "evals_per_step": qev / K, "statuses": qst, "gpu_launches": int(qla),
-                   "loop_time_s_est": len(F) * (qms / K) / 1e3, "roofline": qroof, "clocks": qsampler.summary(),
+                   "loop_time_s_extrapolated": len(F) * (qms / K) / 1e3, "roofline": qroof, "clocks": qsampler.summary(),
                    "launch_shape": {k: qinfo[k] for k in ("x_fwd_tile_rows", "x_tile_rows", "yz_batch_rows")}}
         qp.close()
     if ws == 1:
