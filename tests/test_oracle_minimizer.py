@@ -192,7 +192,7 @@ def test_sweep_opens_the_stoner_wohlfarth_loop_on_both_branches():
 
 
 def test_sweep_is_a_chain_of_fresh_minimisations():
-    """Per field value the driver runs one minimisation from the previous
+    """Per field value the sweep runs one minimisation from the previous
     result with the step-size history restarted (tau = tau0, k = 0); <m> is
     the mean of that result.  Replaying the chain with independent calls
     must give the same states, means and evaluation counts -- carrying tau
