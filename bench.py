@@ -500,8 +500,8 @@ def run_batch(args, ws, rank, local, dev):
     import torch
     from paper_1405_2728_gb300 import inputs, mm
     films = inputs.batch_films(64)
-    prec = mm.MM_FP64 if args.precision == "fp64" else mm.MM_FP32
-    tdt = torch.float64 if prec == mm.MM_FP64 else torch.float32
+    prec = PRECISIONS.get(args.precision, mm.MM_FP64)
+    tdt = torch.float32 if prec == mm.MM_FP32 else torch.float64
     probs = [mm.mm_setup_geometry(mm.make_grid(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz),
                                   mm.make_material(w.Ms, w.A, w.K), prec) for w in films]
     F = films[0].fields()
@@ -536,8 +536,10 @@ def run_batch(args, ws, rank, local, dev):
             return ev
         seq(0, W)
         ev_s, t_s = timed(lambda: seq(W, K))
-        for name, kind in (("branches", mm.MM_BATCH_BRANCHES), ("streams", mm.MM_BATCH_STREAMS),
-                           ("grouped", mm.MM_BATCH_GROUPED)):
+        kinds = [("branches", mm.MM_BATCH_BRANCHES), ("streams", mm.MM_BATCH_STREAMS)]
+        if prec != mm.MM_F32X2:   # grouped launches serve FP64 and FP32 films only
+            kinds.append(("grouped", mm.MM_BATCH_GROUPED))
+        for name, kind in kinds:
             batch = mm.mm_batch_create(probs, kind)
             ms = fresh()
 
@@ -563,7 +565,7 @@ def run_batch(args, ws, rank, local, dev):
     line = {
         "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec == mm.MM_FP64 else "f32", "data": "synthetic",
+        "dtype": DTYPE_LABEL.get(args.precision, "f64"), "data": "synthetic",
         "config": {"workload": "batch64_films", "films": len(films), "cells_min_max_sum": [min(cells), max(cells), sum(cells)],
                    "precision": args.precision,
                    "step": "one field value of the +-50 mT / 2 mT sweep for all 64 films, tol 1e-5; the K timed "
