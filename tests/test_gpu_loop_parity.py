@@ -21,14 +21,20 @@ import os
 
 import numpy as np
 import pytest
+import torch
 
 from paper_1405_2728_gb300 import inputs
 from gpu_cases import dev
 
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-CASES = [("film_128x64x2_loop.json", "film_128x64x2"), ("film_128x64x2_descending.json", "film_128x64x2"),
-         ("film_512x256x4_descending.json", "film_512x256x4")]
+# FP32 is compared on the 128 x 64 x 2 loops; on the 512 x 256 x 4 film its
+# float rounding stalls the step-size sums near the tolerance, and some field
+# values need more than the stored run's 1e5-iteration cap
+CASES = [(f, wl, p) for f, wl, precs in (("film_128x64x2_loop.json", "film_128x64x2", ("fp64", "f32x2", "fp32")),
+                                         ("film_128x64x2_descending.json", "film_128x64x2", ("fp64", "f32x2", "fp32")),
+                                         ("film_512x256x4_descending.json", "film_512x256x4", ("fp64", "f32x2")))
+         for p in precs]
 
 
 def _stored(fname, workload):
@@ -56,17 +62,16 @@ def _switches(b, p):
     return down, up, nd
 
 
-@pytest.mark.parametrize("fname,workload", CASES)
-@pytest.mark.parametrize("precision", ["fp64", "f32x2"])
+@pytest.mark.parametrize("fname,workload,precision", CASES)
 def test_loop_matches_oracle(mmlib, fname, workload, precision):
     w, rec = _stored(fname, workload)
-    prec = mmlib.MM_FP64 if precision == "fp64" else mmlib.MM_F32X2
+    prec = {"fp64": mmlib.MM_FP64, "f32x2": mmlib.MM_F32X2, "fp32": mmlib.MM_FP32}[precision]
     H = np.array(rec["H"])
     n = len(H)
     assert n >= 2 and all(rec["converged"])
     grid = mmlib.make_grid(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz)
     prob = mmlib.mm_setup_geometry(grid, mmlib.make_material(w.Ms, w.A, w.K), prec)
-    m = dev(w.initial_m())
+    m = dev(w.initial_m(), torch.float32 if precision == "fp32" else torch.float64)
     st, mavg, res = mmlib.mm_hysteresis_sweep(prob, m, H, opts=mmlib.make_opts(tol=w.tol, max_iter=rec["max_iter"]))
     prob.close()
     assert st == mmlib.MM_OK and all(r.converged for r in res)
