@@ -51,6 +51,7 @@ enum {
     RED_EAN,         // sum K (1 - (m.u)^2)
     RED_EZ,          // sum m.H_ext
     RED_MX, RED_MY, RED_MZ,  // sum m
+    RED_PAD,         // unused: a CTA's row of partials stays a multiple of 16 bytes
     RED_NSLOT
 };
 

@@ -356,6 +356,7 @@ __global__ void __launch_bounds__(YZBound<T>::v) k_yz(Geom g, FieldPtrs<T, F> P)
 enum { SL_SS = 0, SL_SY = 1, SL_YY = 2, SL_T2 = 3, SL_ET = 4, SL_MX = 5, SL_MY = 6, SL_MZ = 7, NSL = 8 };
 enum { SL_ED = 0, SL_EEX = 1, SL_EAN = 2, SL_EZ = 3 };
 static_assert(NSL <= RED_NSLOT, "partials buffer holds RED_NSLOT doubles per CTA");
+static_assert(NSL % 2 == 0 && RED_NSLOT % 2 == 0, "the last CTA reads the partials in 16-byte pairs");
 
 // accumulator: double on the double path, a compensated float pair on the float path
 template <typename T> struct Acc;
@@ -441,21 +442,49 @@ __device__ void finish_iteration(const Geom &g, double *partials, int nblk, MinS
                                  cudaGraphConditionalHandle h, int use_cond, int body_kernels)
 {
     const int lane = threadIdx.x & 31;
+    // lane l sums blocks l, l + 32, l + 64, ... of every slot in that order;
+    // the loads of FB blocks (all slots, 16-byte reads) are issued before any
+    // is added, so the wait is one L2 round trip per FB blocks, not one per
+    // block and slot
+    constexpr int FB = 2;
+    double v[NSL];
+#pragma unroll
+    for (int s = 0; s < NSL; ++s) v[s] = 0.0;
+    auto fold = [&](const double2 *x) {
+#pragma unroll
+        for (int s = 0; s < NSL; ++s) {
+            const double xs = (s & 1) ? x[s / 2].y : x[s / 2].x;
+            v[s] = (MODE == MODE_MIN && s == SL_T2) ? fmax(v[s], xs) : v[s] + xs;
+        }
+    };
+    int b = lane;
+    for (; b + (FB - 1) * 32 < nblk; b += FB * 32) {
+        double2 x[FB][NSL / 2];
+#pragma unroll
+        for (int i = 0; i < FB; ++i)
+#pragma unroll
+            for (int q = 0; q < NSL / 2; ++q)
+                x[i][q] = __ldcg(reinterpret_cast<const double2 *>(partials + (long)(b + 32 * i) * RED_NSLOT) + q);
+#pragma unroll
+        for (int i = 0; i < FB; ++i) fold(x[i]);
+    }
+    for (; b < nblk; b += 32) {
+        double2 x[NSL / 2];
+#pragma unroll
+        for (int q = 0; q < NSL / 2; ++q) x[q] = __ldcg(reinterpret_cast<const double2 *>(partials + (long)b * RED_NSLOT) + q);
+        fold(x);
+    }
     double tot[NSL];
 #pragma unroll
     for (int s = 0; s < NSL; ++s) {
         const bool isMax = (MODE == MODE_MIN && s == SL_T2);
-        double v = 0.0;
-        for (int b = lane; b < nblk; b += 32) {
-            const double x = __ldcg(partials + (long)b * RED_NSLOT + s);
-            v = isMax ? fmax(v, x) : v + x;
-        }
+        double w = v[s];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const double y = __shfl_down_sync(0xffffffffu, v, o);
-            v = isMax ? fmax(v, y) : v + y;
+            const double y = __shfl_down_sync(0xffffffffu, w, o);
+            w = isMax ? fmax(w, y) : w + y;
         }
-        tot[s] = v;
+        tot[s] = w;
     }
     if (lane != 0) return;
     const double V = g.dx * g.dy * g.dz, Ms = g.Ms, cE = MM_MU0 * Ms * V;
