@@ -127,8 +127,10 @@ template <typename T, typename F> cudaError_t configure_t(const Geom &g, size_t 
 // Launch-shape autotuner: time every admissible rows-per-tile of the
 // x-forward kernel and, separately, of the x-inverse kernel (the two are
 // independent: the spectrum layout does not depend on the tile), and every
-// rows-per-batch RB of the y-z kernel, on this problem's own buffers (three
-// repetitions, best taken); keep the fastest of each.  The kernels run in
+// rows-per-batch RB of the y-z kernel, on this problem's own buffers
+// (MM_TUNE_REPS repetitions, best taken: candidates within a few percent of
+// each other otherwise swap places from run to run); keep the fastest of each.
+#define MM_TUNE_REPS 5  The kernels run in
 // their minimiser modes on the zeroed state of a fresh problem.
 template <typename T, typename F> cudaError_t autotune_t(mm_problem *p, const int *tys, int nty, const int *rbs, int nrb,
                                              cudaStream_t s)
@@ -162,7 +164,7 @@ template <typename T, typename F> cudaError_t autotune_t(mm_problem *p, const in
             if (which == 0) { g.TYF = tys[i]; g.ltyf = mm_ilog2(g.TYF); }
             else { g.TY = tys[i]; g.lty = mm_ilog2(g.TY); }
             float tmin = 1e30f;
-            for (int r = 0; r < 3 && !e; ++r) {
+            for (int r = 0; r < MM_TUNE_REPS && !e; ++r) {
                 cudaEventRecord(a, s);
                 if (which == 0) launch_xfwd<T, F, true>(g, P, s);
                 else launch_xinv<T, F, MODE_MIN>(g, P, s, nullptr, 0, 0);
@@ -182,7 +184,7 @@ template <typename T, typename F> cudaError_t autotune_t(mm_problem *p, const in
     for (int i = 0; i < nrb && !e && !g.bulk; ++i) {
         g.RB = rbs[i];
         float tmin = 1e30f;
-        for (int r = 0; r < 3 && !e; ++r) {
+        for (int r = 0; r < MM_TUNE_REPS && !e; ++r) {
             cudaEventRecord(a, s);
             e = launch_yz_any<T, F>(g, P, s);
             cudaEventRecord(b, s);
