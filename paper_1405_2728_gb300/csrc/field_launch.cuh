@@ -130,8 +130,9 @@ template <typename T, typename F> cudaError_t configure_t(const Geom &g, size_t 
 // rows-per-batch RB of the y-z kernel, on this problem's own buffers
 // (MM_TUNE_REPS repetitions, best taken: candidates within a few percent of
 // each other otherwise swap places from run to run); keep the fastest of each.
-#define MM_TUNE_REPS 5  The kernels run in
-// their minimiser modes on the zeroed state of a fresh problem.
+// The kernels run in their minimiser modes on the zeroed state of a fresh
+// problem.
+#define MM_TUNE_REPS 5
 template <typename T, typename F> cudaError_t autotune_t(mm_problem *p, const int *tys, int nty, const int *rbs, int nrb,
                                              cudaStream_t s)
 {
