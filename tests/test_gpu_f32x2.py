@@ -48,6 +48,57 @@ def test_energy_f32x2(mmlib):
         assert abs(E[i] - ref[k]) <= 1e-11 * scale, (k, E[i], ref[k])
 
 
+def test_f32x2_per_cell_material(mmlib):
+    """Per-cell K and easy axes stay double and enter the double-word local
+    terms converted per load: the field (host buffers, staged by the library),
+    the energies and 25 minimiser steps against the oracle."""
+    nx, ny, nz = 24, 12, 3
+    shape = (nz, ny, nx)
+    K = inputs.uniform(3, nx * ny * nz, 1e3, 5e4).reshape(shape)
+    u = inputs.random_unit_m(shape, 17)
+    prob, oprob = make_pair(mmlib, nx, ny, nz, CELL, K_cell=K, u_cell=u, precision=mmlib.MM_F32X2)
+    m = inputs.random_unit_m(shape, 18)
+    H = np.zeros((3,) + shape)
+    mmlib.mm_heff(prob, m, (0.0, 3e3, 0.0), H)
+    demag = om.Demag(oprob)
+    assert rel_l2(H, om.heff(oprob, m, (0.0, 3e3, 0.0), demag)) <= 1e-10
+    E = mmlib.mm_energy(prob, dev(m), (0.0, 3e3, 0.0))
+    ref = om.energy(oprob, m, (0.0, 3e3, 0.0), demag)
+    keys = ["demag", "exchange", "anisotropy", "zeeman", "total"]
+    scale = max(abs(ref[k]) for k in keys)
+    for i, k in enumerate(keys):
+        assert abs(E[i] - ref[k]) <= 1e-11 * scale, (k, E[i], ref[k])
+    mg = dev(m)
+    st, r = mmlib.mm_minimize(prob, mg, (0.0, 3e3, 0.0), mmlib.make_opts(tol=0.0, max_iter=25))
+    assert st == mmlib.MM_ERR_NOT_CONVERGED and r.iters == 25
+    ref_m = om.minimize(oprob, m, (0.0, 3e3, 0.0), demag, tol=0.0, max_iter=25).m
+    assert rel_l2(mg.cpu().numpy(), ref_m) <= 1e-7
+
+
+def test_f32x2_inspect_returns_the_iterates_and_their_sums(mmlib):
+    """mm_min_inspect on a double-word problem: the iterates and gradients
+    come back as the double nearest to each pair (m_k equal to what the
+    minimisation returned), and the step-size sums of Eq. (stepsize), formed
+    by the kernels in double-word arithmetic, agree with a float64 reduction
+    of those doubles (their rounding to double moves s and y by ~1e-16 of m)."""
+    w = inputs.film_128x64x2()
+    prob, _ = make_pair(mmlib, w.nx, w.ny, w.nz, (w.dx, w.dy, w.dz), Ms=w.Ms, A=w.A, K=w.K,
+                        precision=mmlib.MM_F32X2)
+    m = dev(w.initial_m())
+    mmlib.mm_minimize(prob, m, w.fields()[30], mmlib.make_opts(tol=0.0, max_iter=12))
+    bufs = [torch.empty(prob.shape, dtype=torch.float64, device="cuda") for _ in range(4)]
+    stt = mmlib.mm_min_inspect(prob, *bufs)
+    assert stt["k"] == 12
+    mk, mp, gk, gp = (b.cpu().numpy() for b in bufs)
+    assert np.array_equal(mk, m.cpu().numpy())
+    assert np.max(np.abs(np.linalg.norm(mk, axis=0) - 1)) < 1e-13
+    s_, y_ = mk - mp, gk - gp
+    ss, sy, yy = float(np.sum(s_ * s_)), float(np.sum(s_ * y_)), float(np.sum(y_ * y_))
+    assert abs(stt["ss"] - ss) <= 1e-8 * ss
+    assert abs(stt["yy"] - yy) <= 1e-8 * yy
+    assert abs(stt["sy"] - sy) <= 1e-8 * np.sqrt(ss * yy)
+
+
 @pytest.mark.parametrize("step", [0, 1])
 def test_fixed_steps_f32x2_follow_the_oracle(mmlib, step):
     w = inputs.film_32x16x1()
