@@ -360,24 +360,24 @@ def run_full_loop(args, w, prob, m, F, opts, stream, tdt, esz, info, dev):
     return 0
 
 
-def run_mixed_loop(args, w, dev):
-    """One whole loop with mm_hysteresis_sweep_mixed: per field value FP32 to
-    --mixed-tol, then FP64 to the workload's tolerance; timed with CUDA events."""
+def measure_mixed_loop(w, dev, hi_name, tol_lo, max_iter, warmup):
+    """One whole loop with mm_hysteresis_sweep_mixed (per field value FP32 to
+    tol_lo, then hi_name, FP64 or f32x2, to the workload's tolerance), timed
+    with CUDA events after a warm-up over the first field values.  Returns
+    the loop's time, evaluations, switching field and clocks."""
     import torch
     from paper_1405_2728_gb300 import inputs, mm
     grid = mm.make_grid(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz)
     mat = mm.make_material(w.Ms, w.A, w.K, K_cell=w.K_cell, u_cell=w.u_cell)
     lo = mm.mm_setup_geometry(grid, mat, mm.MM_FP32)
-    hi = mm.mm_setup_geometry(grid, mat, PRECISIONS[args.mixed_hi])
+    hi = mm.mm_setup_geometry(grid, mat, PRECISIONS[hi_name])
     F = w.fields()
-    if args.mixed_tol is None:
-        args.mixed_tol = 1e-4 if args.mixed_hi == "f32x2" else 3e-5
-    o_lo = mm.make_opts(tol=args.mixed_tol, max_iter=20000)
-    o_hi = mm.make_opts(tol=w.tol, max_iter=args.max_iter)
+    o_lo = mm.make_opts(tol=tol_lo, max_iter=20000)
+    o_hi = mm.make_opts(tol=w.tol, max_iter=max_iter)
     stream = torch.cuda.current_stream(dev)
     m0 = torch.from_numpy(w.initial_m()).to(device=dev, dtype=torch.float64).contiguous()
     m = m0.clone()
-    mm.mm_hysteresis_sweep_mixed(lo, hi, m, F[: args.warmup], opts_lo=o_lo, opts_hi=o_hi, stream=stream)
+    mm.mm_hysteresis_sweep_mixed(lo, hi, m, F[:warmup], opts_lo=o_lo, opts_hi=o_hi, stream=stream)
     m.copy_(m0)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(int(str(dev).split(":")[-1] or 0))
@@ -397,20 +397,30 @@ def run_mixed_loop(args, w, dev):
     while nd < len(h) and h[nd] < h[nd - 1]:
         nd += 1
     sw = [float(h[i]) for i in range(1, nd) if p[i] < 0]
-    line = {"metric": METRIC, "value": (ev_lo + ev_hi) / sec, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
-            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+" + DTYPE_LABEL[args.mixed_hi], "data": "synthetic",
-            "config": {"workload": w.name, "cells": [w.nx, w.ny, w.nz], "precision": "mixed",
-                       "step": f"one whole loop: {len(F)} field values, FP32 to tol {args.mixed_tol:g} "
-                               f"then {args.mixed_hi} to tol {w.tol:g}"},
-            "loop_time_s": sec, "loop_evals_fp32": int(ev_lo), "loop_evals_fp64": int(ev_hi),
+    lo.close()
+    hi.close()
+    return {"loop_time_s": sec, "loop_evals_fp32": int(ev_lo), "loop_evals_fp64": int(ev_hi),
             "converged_field_values": int(sum(r.converged for r in rh)), "field_values": len(F),
             "status": int(st), "H_sw_mT": sw[0] if sw else None,
             "gpu_launches": int(sum(r.kernel_launches for r in rl) + sum(r.kernel_launches for r in rh)),
             "clocks": sampler.summary()}
+
+
+def run_mixed_loop(args, w, dev):
+    """One whole loop with mm_hysteresis_sweep_mixed: per field value FP32 to
+    --mixed-tol, then --mixed-hi to the workload's tolerance."""
+    if args.mixed_tol is None:
+        args.mixed_tol = 1e-4 if args.mixed_hi == "f32x2" else 3e-5
+    r = measure_mixed_loop(w, dev, args.mixed_hi, args.mixed_tol, args.max_iter, args.warmup)
+    F = w.fields()
+    line = {"metric": METRIC, "value": (r["loop_evals_fp32"] + r["loop_evals_fp64"]) / r["loop_time_s"], "unit": UNIT,
+            "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": r["loop_time_s"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+" + DTYPE_LABEL[args.mixed_hi], "data": "synthetic",
+            "config": {"workload": w.name, "cells": [w.nx, w.ny, w.nz], "precision": "mixed",
+                       "step": f"one whole loop: {len(F)} field values, FP32 to tol {args.mixed_tol:g} "
+                               f"then {args.mixed_hi} to tol {w.tol:g}"},
+            **r}
     print(json.dumps(line))
-    lo.close()
-    hi.close()
     return 0
 
 
@@ -683,6 +693,8 @@ def main():
                     help="precision of the second (final-tolerance) phase of --precision mixed")
     ap.add_argument("--workload", default="film_512x256x4")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-loop", action="store_true",
+                    help="leave out the measured whole loop of the default 512x256x4 line (about a minute)")
     ap.add_argument("--adjoint", action="store_true",
                     help="time the implicit adjoint (differentiation extension) on the 128x64x2 film instead")
     ap.add_argument("--only", action="store_true",
@@ -914,6 +926,11 @@ def main():
             "demag_convolution_ms": theirs, "ours_full_evaluation_ms": ours,
             "note": "torch.fft (cuFFT) demag convolution alone vs this library's whole evaluation "
                     "(step, convolution, local terms, step-size sums); comparison only"}
+    if not args.no_loop and ws == 1 and not args.only and args.workload == "film_512x256x4":
+        # the metric's loop time, measured: the fastest loop of FP64 accuracy (FP32, then
+        # double-word from a 1e-4 hand-over), every field value of the sweep in one call
+        line["loop_measured"] = {"sweep": "mm_hysteresis_sweep_mixed, FP32 then f32x2 (hand-over tol 1e-4)",
+                                 **measure_mixed_loop(w, dev, "f32x2", 1e-4, args.max_iter, args.warmup)}
     if not args.no_cpu_baseline and ws == 1 and args.workload in inputs.BULK_WORKLOADS:
         line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": "not run: the oracle's quad-precision tensor on the (n+1)^3 lattice of "
